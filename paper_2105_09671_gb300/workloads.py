@@ -1,0 +1,79 @@
+"""Seeded synthetic workloads: grid recipes and generic random fields.
+
+This module holds parameters and seeded random arrays only -- none of the
+scheme's arithmetic -- so that the CUDA path and the CPU oracle can both be
+fed from it without sharing any of the method.
+
+Recipes follow the paper's setup (Section 2 and 3): unit domain, cell size
+h = 1/Nx, time step dt = 0.1 h^2, interface width eps given per workload.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    shape: tuple          # (ny, nx) or (nz, ny, nx)
+    eps: float
+    steps: int
+    init: str             # "sphere" (circle in 2D) or "random"
+    r0: float = 0.25
+    seed: int = 0
+
+    @property
+    def ndim(self) -> int:
+        return len(self.shape)
+
+    @property
+    def nx(self) -> int:
+        return self.shape[-1]
+
+    @property
+    def h(self) -> float:
+        return 1.0 / self.nx
+
+    @property
+    def dt(self) -> float:
+        return 0.1 * self.h * self.h
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.shape))
+
+
+# 2D circle, 64^2, FP64 parity case; radius checked against the shrinking law.
+CIRCLE_64 = Workload("circle2d_64", (64, 64), eps=0.015, steps=1000, init="sphere")
+# 2D phase separation, 4096^2, random initial state in [-0.1, 0.1).
+SEPARATION_4096 = Workload("separation2d_4096", (4096, 4096), eps=0.004, steps=5000,
+                           init="random", seed=0)
+# 3D sphere, 512^3 (the FP32 / FP16-storage throughput workload).
+SPHERE_512 = Workload("sphere3d_512", (512, 512, 512), eps=0.003, steps=2000, init="sphere")
+# 3D sphere at 256^3 for the FP16-storage error report against FP64.
+SPHERE_256 = Workload("sphere3d_256", (256, 256, 256), eps=0.003, steps=2000, init="sphere")
+
+
+def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Generic seeded FP64 field, uniform in [lo, hi) (numpy PCG64)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=shape)
+
+
+def smooth_field(shape, seed: int, modes: int = 4, amp: float = 0.9) -> np.ndarray:
+    """Seeded smooth field: a sum of a few random cosine modes on cell centres,
+    scaled to max |phi| <= amp.  Used as a generic parity input with interfaces."""
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in shape], indexing="ij")
+    f = np.zeros(shape)
+    for _ in range(modes):
+        k = rng.integers(1, 6, size=len(shape))
+        ph = rng.uniform(0, 2 * np.pi, size=len(shape))
+        term = np.ones(shape)
+        for g, kk, pp in zip(grids, k, ph):
+            term = term * np.cos(np.pi * kk * g + pp)
+        f += rng.uniform(-1, 1) * term
+    m = np.max(np.abs(f))
+    return amp * f / m if m > 0 else f

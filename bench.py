@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Allen-Cahn stepper.
+
+One benchmark step is one whole job of the 3D mean-curvature workload:
+device-side sphere initial condition on a 512^3 grid (h = 1/512,
+dt = 0.1 h^2, eps = 0.003), 2000 explicit Euler steps in FP32 storage and
+arithmetic, then the FP64 energy / phase-volume reduction read back to the
+host.  Inputs are resident in HBM; two 512 MiB buffers are far larger than
+L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(one per rank, weak scaling); the only cross-rank traffic is the barrier and
+the max-over-ranks of the timed interval.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s + HBM roofline %; speedup vs plain FP32 at ≤1e-3 rel-L2"
+UNIT = "Gcell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------ distributed --
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("AC_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def dist_barrier(ws, device=None):
+    if ws > 1:
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl" and device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def dist_max(ws, value: float, device=None) -> float:
+    """Maximum of a float over all ranks (the slowest replica sets the time)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="ac_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sms, maxes, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sms.append(float(parts[0]))
+                    maxes.append(float(parts[1]))
+                    power.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[4:8]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sms if s >= 0.5 * max(sms)] or sms
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(maxes),
+                "reasons": sorted(reasons), "samples": len(sms),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ peaks ---
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel: str, source: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        with open(os.path.join(ROOT, "paper_2105_09671_gb300", "csrc", source), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError, AttributeError):
+        return None
+    if not rec or rec.get("source_sha256") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# -------------------------------------------------------------- workloads --
+def workload(name: str):
+    from paper_2105_09671_gb300 import workloads as wl
+    if name == "sphere512":
+        return wl.SPHERE_512, "f32", "stream3d_k<float>", "k_stream3d.cu"
+    if name == "separation4096":
+        return wl.SEPARATION_4096, "f32", "stream2d_k<float>", "k_stream2d.cu"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def init_field(sim, w):
+    if w.init == "sphere":
+        sim.init_sphere(r0=w.r0)
+    else:
+        sim.init_random(seed=w.seed, amplitude=0.1)
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def oracle_sample(w, target_s: float, max_steps: int = 20):
+    """Time the FP64 oracle on the same grid for a bounded number of steps."""
+    import numpy as np
+    import oracle
+    if w.init == "sphere":
+        phi0 = oracle.init_sphere(w.shape, w.h, w.r0, w.eps).astype(np.float32).astype(np.float64)
+    else:
+        phi0 = oracle.init_random(w.shape, seed=w.seed).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    phi = oracle.step(phi0, w.h, w.eps, w.dt, 1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, target_s / max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.step(phi, w.h, w.eps, w.dt, steps)
+    dt_s = time.perf_counter() - t0
+    return steps, dt_s, oracle.num_threads()
+
+
+def run_reference(args, ws, rank):
+    """The oracle arm: the FP64 C oracle on the host cores, same workload."""
+    if rank != 0:
+        return
+    import oracle
+    w, dtype, _, _ = workload(args.workload)
+    import numpy as np
+    phi0 = (oracle.init_sphere(w.shape, w.h, w.r0, w.eps) if w.init == "sphere"
+            else oracle.init_random(w.shape, seed=w.seed)).astype(np.float32).astype(np.float64)
+    steps_per = args.ref_steps
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.step(phi0, w.h, w.eps, w.dt, steps_per)
+        dt_s = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt_s)
+    total = sum(times)
+    value = w.cells * steps_per * len(times) / total / 1e9
+    cores = oracle.num_threads()
+    sample = (f"{w.name}: {w.cells} cells x {steps_per} Euler step(s) per benchmark step "
+              f"(the full job is {w.steps} steps), FP64 oracle, OpenMP")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ ours ---
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import paper_2105_09671_gb300 as ac
+
+    w, dtype, kname, ksrc = workload(args.workload)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device)
+    sim = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype, device=device, stream=stream)
+    if args.k:
+        sim.set_schedule(ac.AC_VARIANT_STREAM if args.k > 0 else ac.AC_VARIANT_DIRECT, abs(args.k))
+    variant, k = sim.schedule()
+    es = {"f64": 8, "f32": 4, "f16s": 2}[dtype]
+    field_bytes = w.cells * es
+
+    def job():
+        init_field(sim, w)
+        sim.step(w.steps)
+        return sim.observe()
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize(device)
+
+    n_ev = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_ev)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dist_barrier(ws, device)
+    torch.cuda.synchronize(device)
+    l0 = sim.launch_count()
+    start.record(stream)
+    stencil_launches = 0
+    for i in range(n_ev):
+        ev[i][0].record(stream)
+        init_field(sim, w)
+        ev[i][1].record(stream)
+        c0 = sim.launch_count()
+        sim.step(w.steps)
+        stencil_launches += sim.launch_count() - c0
+        ev[i][2].record(stream)
+        obs = sim.observe()
+    end.record(stream)
+    torch.cuda.synchronize(device)
+    dist_barrier(ws, device)
+    launches = sim.launch_count() - l0
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    elapsed_ms = dist_max(ws, elapsed_ms, device)
+    stencil_ms = sum(ev[i][1].elapsed_time(ev[i][2]) for i in range(n_ev))
+    updates = w.cells * w.steps * args.steps * ws
+    value = updates / (elapsed_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel: algorithmic bytes per launch (read phi
+    # once and write it once, whatever k) over its live average duration
+    avg_launch_s = stencil_ms / 1e3 / max(1, stencil_launches)
+    alg_bytes = 2 * field_bytes
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = recorded_traffic(f"{kname} k={k}", ksrc) if variant == ac.AC_VARIANT_STREAM else None
+
+    # end to end through the public API with host buffers: H2D of the initial
+    # state from pinned memory, the steps, D2H of the final field + the energy
+    host_in = torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True)
+    host_out = torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True)
+    init_field(sim, w)
+    with torch.cuda.stream(stream):
+        host_in.copy_(sim.phi, non_blocking=True)
+    stream.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    dist_barrier(ws, device)
+    torch.cuda.synchronize(device)
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_s.record(stream)
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            sim.phi.copy_(host_in, non_blocking=True)
+        sim.step(w.steps)
+        with torch.cuda.stream(stream):
+            host_out.copy_(sim.phi, non_blocking=True)
+        obs_e2e = sim.observe()
+    e_e.record(stream)
+    torch.cuda.synchronize(device)
+    e2e_ms = dist_max(ws, e_s.elapsed_time(e_e), device)
+    e2e_value = w.cells * w.steps * e2e_steps * ws / (e2e_ms / 1e3) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.shape), "euler_steps_per_job": w.steps,
+                   "eps": w.eps, "h": w.h, "dt": w.dt, "init": w.init,
+                   "schedule": {"variant": "stream" if variant == 2 else "direct", "k": k},
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "no flush: two field buffers of %d MiB each exceed L2" % (field_bytes >> 20)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"{kname} k={k}", "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                     "effective_frac_k1": value / ws * 2 * es / peak},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
+                "d2h_bytes_per_step": field_bytes + 24},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "result": {"energy": obs[0], "phase_volume": obs[1], "nonfinite": obs[2],
+                   "radius": ((3 * obs[1]) / (4 * math.pi)) ** (1 / 3) if w.ndim == 3 else math.sqrt(obs[1] / math.pi)},
+    }
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        steps, secs, cores = oracle_sample(w, args.cpu_seconds)
+        out["cpu_baseline"] = {
+            "value": w.cells * steps / secs / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{w.name}: all {w.cells} cells, {steps} Euler steps of the FP64 oracle "
+                      f"(the job runs {w.steps}); {secs:.1f} s"}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sphere512", choices=["sphere512", "separation4096"])
+    ap.add_argument("--k", type=int, default=0,
+                    help="force the temporal-block depth (negative: direct kernel, k=1)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-steps", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # host-only arm: rank 0 runs the oracle, other ranks leave at once
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    ws, rank, local = dist_setup()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * ac.h -- C ABI of the GB300 (sm_103a) Allen-Cahn stepper.
+ *
+ * The library advances the explicit finite-difference Allen-Cahn scheme of
+ * Kim, "Fast Numerical Simulation of Allen-Cahn Equation" (arXiv 2105.09671):
+ *
+ *   phi_t = -F'(phi)/eps^2 + Lap phi,  F(phi) = (phi^2 - 1)^2 / 4  (Eq. oriACeq)
+ *   phi^{n+1} = phi^n + dt ((phi^n - (phi^n)^3)/eps^2 + Lap_h phi^n)  (Eq. pytorchACeq)
+ *
+ * on a cell-centred grid with h = 1/Nx, zero-Neumann boundaries realised by
+ * replicating the boundary cell into a ghost layer (Section 2), a 5-point
+ * (2D) or 7-point (3D) Laplacian and forward Euler with dt = 0.1 h^2.
+ *
+ * Conventions for every entry point:
+ *   - All functions return an int status: AC_OK (0) or one of AC_ERR_*.
+ *     No C++ exception crosses this boundary.  ac_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.
+ *   - Device pointers are plain CUDA global-memory addresses owned by the
+ *     caller; the library never frees them.  The library allocates only
+ *     small internal reduction/status buffers in ac_create and releases them
+ *     in ac_destroy.
+ *   - Work is stream-ordered on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  Only the functions
+ *     documented as synchronising wait for the stream.
+ *   - Not thread-safe per context: one host thread drives one context at a
+ *     time.  Different contexts are independent.
+ */
+#ifndef AC_H_
+#define AC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status ---- */
+enum {
+  AC_OK = 0,
+  AC_ERR_INVALID = 1,     /* bad descriptor, pointer, alignment or argument */
+  AC_ERR_CUDA = 2,        /* a CUDA runtime / driver call failed            */
+  AC_ERR_NONFINITE = 3,   /* the field holds NaN or Inf                     */
+  AC_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired             */
+  AC_ERR_UNSUPPORTED = 5, /* valid request this build cannot serve          */
+  AC_ERR_NOMEM = 6        /* internal allocation failed                     */
+};
+
+/* ------------------------------------------------------ storage types ---- */
+typedef enum {
+  AC_F64 = 0,  /* FP64 storage, FP64 arithmetic                        */
+  AC_F32 = 1,  /* FP32 storage, FP32 arithmetic                        */
+  AC_F16S = 2  /* FP16 storage (IEEE binary16), FP32 arithmetic; values
+                  are rounded to nearest-even only when written to memory */
+} ac_dtype;
+
+/* -------------------------------------------------------- descriptor ---- */
+/* One simulation grid (Section 2): Nx x Ny (x Nz) cells of size h.
+ *
+ * Layout of phi in device memory: row-major, x fastest.  Cell (i, j, k),
+ * 0-based, lives at element  (k * ny + j) * pitch_x + i.
+ *
+ *   ndim     2 or 3.  For ndim == 2, nz must be 1.
+ *   dtype    an ac_dtype.
+ *   nx,ny,nz number of cells per axis, each >= 1.
+ *   pitch_x  elements between consecutive rows; pitch_x >= nx and
+ *            pitch_x * element_size is a multiple of 16 bytes.
+ *   h        cell size (the paper uses h = 1/Nx).
+ *   eps      interface-thickness parameter epsilon > 0 (Eq. emvalue gives
+ *            the paper's choice eps_m = h m / (2 sqrt(2) atanh(0.9))).
+ *   dt       time step > 0.  The paper uses dt = 0.1 h^2.  The library
+ *            requires dt <= h^2 / (2 ndim) (stability of the explicit
+ *            Laplacian) and dt <= eps^2 (reaction step alpha = dt/eps^2
+ *            at most 1); anything else is AC_ERR_INVALID.
+ */
+typedef struct {
+  int32_t ndim;
+  int32_t dtype;
+  int64_t nx, ny, nz;
+  int64_t pitch_x;
+  double h, eps, dt;
+} ac_grid_desc;
+
+typedef struct ac_ctx ac_ctx; /* opaque */
+
+/* Bytes of device workspace ac_create needs: one more field of the same
+ * layout (the ping-pong partner of phi).  Writes the count to *out. */
+int ac_workspace_bytes(const ac_grid_desc *desc, size_t *out);
+
+/* Create a stepping context for the field phi_dev (laid out as described
+ * by desc) with workspace_dev of at least ac_workspace_bytes() bytes.
+ * Both pointers must be 16-byte aligned device addresses and must not
+ * overlap.  cuda_stream is the cudaStream_t all later work is ordered on.
+ * The context keeps the pointers; the caller keeps ownership and must keep
+ * them alive until ac_destroy.  The device current at this call is used. */
+int ac_create(const ac_grid_desc *desc, void *phi_dev, void *workspace_dev,
+              void *cuda_stream, ac_ctx **out);
+
+/* Advance phi by n >= 0 explicit Euler steps of Eq. (pytorchACeq) with the
+ * zero-Neumann ghosts of Section 2.  Asynchronous on the context's stream;
+ * when the work completes the result is in phi_dev (the workspace holds
+ * intermediate states).  The schedule (kernel variant and temporal-block
+ * depth k: steps advanced per HBM round trip) is the one chosen by
+ * ac_set_schedule / ac_autotune, else a built-in default. */
+int ac_step(ac_ctx *ctx, int64_t n);
+
+/* Discrete Ginzburg-Landau energy of the current phi, summed in FP64:
+ *   E_h = h^d [ sum_cells F(phi)/eps^2 + 1/2 sum_interior faces ((phi_a - phi_b)/h)^2 ]
+ * (not defined in the paper; its gradient is -h^d times the right-hand side
+ * of Eq. pytorchACeq, so the scheme decreases it).  Synchronises the stream.
+ * Returns AC_ERR_NONFINITE (and still writes *out) if phi holds NaN/Inf. */
+int ac_energy(ac_ctx *ctx, double *out);
+
+/* Phase volume V = h^d sum (1 + phi)/2 in FP64 (area in 2D).  The
+ * equivalent radius sqrt(V/pi) (2D) or (3V/(4 pi))^(1/3) (3D) is compared
+ * with the shrinking law r(t)^2 = r0^2 + 2(1 - d) t (Eq. exactradiusEQ).
+ * Synchronises the stream. */
+int ac_phase_volume(ac_ctx *ctx, double *out);
+
+/* Energy, volume and the count of non-finite cells from one pass over phi,
+ * written to out[0], out[1], out[2] (the count as a double).  Synchronises. */
+int ac_observe(ac_ctx *ctx, double out[3]);
+
+/* Initial conditions of Section 3.1, generated on the device into phi.
+ * ac_init_sphere: phi = tanh((r0 - |x - c|)/(sqrt(2) eps)) at cell centres
+ *   x_i = lower + (i + 0.5) h (circle in 2D; cz is ignored), evaluated in
+ *   FP64 and rounded once to the storage type.
+ * ac_init_random: phi = amplitude * (2 u - 1), u = (z >> 11) 2^-53, where z
+ *   is output number (c + 1) of the SplitMix64 sequence seeded with `seed`
+ *   (Steele, Lea, Flood 2014) and c is the cell's linear index x + nx (y +
+ *   ny z) (pitch excluded).  The paper's random state is amplitude 0.1.
+ * Both are asynchronous on the context's stream. */
+int ac_init_sphere(ac_ctx *ctx, double lower_x, double lower_y, double lower_z,
+                   double cx, double cy, double cz, double r0);
+int ac_init_random(ac_ctx *ctx, uint64_t seed, double amplitude);
+
+/* ------------------------------------------------------- scheduling ---- */
+/* Kernel variants selectable with ac_set_schedule. */
+enum {
+  AC_VARIANT_AUTO = 0,    /* autotuned choice if ac_autotune ran, else default */
+  AC_VARIANT_DIRECT = 1,  /* one step per launch, neighbours read from global
+                             memory with clamped indices (k must be 1)         */
+  AC_VARIANT_STREAM = 2   /* TMA-staged streaming kernel with temporal blocking:
+                             2D warp strips streaming along y with warp-shuffle
+                             x neighbours; 3D xy tiles streaming along z with
+                             shared-memory x/y neighbours; k steps per pass    */
+};
+
+/* Force the kernel variant and temporal-block depth k (1..AC_MAX_K) used by
+ * ac_step.  variant = AC_VARIANT_AUTO with k = 0 restores the default. */
+#define AC_MAX_K 8
+int ac_set_schedule(ac_ctx *ctx, int32_t variant, int32_t k);
+int ac_get_schedule(ac_ctx *ctx, int32_t *variant, int32_t *k);
+
+/* Time the candidate (variant, k) schedules on the context's own buffers
+ * with CUDA events (about steps_per_trial steps each) and keep the fastest.
+ * phi is saved to a temporary device buffer that this call allocates and
+ * frees, and restored after every trial, so the field is unchanged.  The
+ * choice is cached per (ndim, dtype, log2 of the cell count, device) for
+ * the process lifetime; later contexts of the same class reuse it without
+ * timing.  Synchronises the stream. */
+int ac_autotune(ac_ctx *ctx, int64_t steps_per_trial);
+
+/* Replay ac_step through a CUDA graph: the first ac_step(n) after enabling
+ * (or after the schedule or n changes) captures the whole launch sequence
+ * for n steps into a graph; later calls with the same n launch the graph
+ * (one launch instead of one per pass).  Needs a non-default stream
+ * (AC_ERR_UNSUPPORTED otherwise).  enable = 0 drops the graph. */
+int ac_set_graph(ac_ctx *ctx, int32_t enable);
+
+/* Device-side error word of the context (bounded waits that expired set
+ * it).  Synchronises, returns AC_ERR_TIMEOUT if set and clears it. */
+int ac_status(ac_ctx *ctx);
+
+/* Number of CUDA kernels this context has enqueued on its stream since
+ * ac_create (stencil passes, reductions, initial conditions; a graph replay
+ * counts the kernels it contains).  The ws -> phi copy that ends an odd
+ * number of single-step passes is a copy, not a kernel, and is not counted. */
+int ac_launch_count(ac_ctx *ctx, int64_t *out);
+
+/* Release the context's internal buffers.  Does not touch phi/workspace.
+ * Synchronises the stream first.  NULL is accepted. */
+int ac_destroy(ac_ctx *ctx);
+
+/* Message for the last failure on this thread ("" if none). */
+const char *ac_last_error(void);
+
+/* Library version string, e.g. "1.0.0 sm_103a". */
+const char *ac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AC_H_ */

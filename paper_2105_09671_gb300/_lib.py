@@ -1,0 +1,196 @@
+"""ctypes binding of ``libac.so`` (the C ABI declared in include/ac.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name.  Device memory and streams come from PyTorch; the library
+receives plain pointers.  There is no fallback: if the CUDA library cannot
+be loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+AC_OK = 0
+AC_ERR_INVALID = 1
+AC_ERR_CUDA = 2
+AC_ERR_NONFINITE = 3
+AC_ERR_TIMEOUT = 4
+AC_ERR_UNSUPPORTED = 5
+AC_ERR_NOMEM = 6
+
+AC_F64, AC_F32, AC_F16S = 0, 1, 2
+AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM = 0, 1, 2
+AC_MAX_K = 8
+
+EXPORTED = (
+    "ac_workspace_bytes", "ac_create", "ac_step", "ac_energy", "ac_phase_volume", "ac_observe",
+    "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_autotune",
+    "ac_set_graph", "ac_status", "ac_launch_count", "ac_destroy", "ac_last_error", "ac_version",
+)
+
+
+class AcGridDesc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("nz", ctypes.c_int64),
+        ("pitch_x", ctypes.c_int64),
+        ("h", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("dt", ctypes.c_double),
+    ]
+
+
+class AcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[ac error {code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libac.so (building it first if missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise AcError(AC_ERR_UNSUPPORTED, f"CUDA library not built: {path}")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    dp = ctypes.POINTER(AcGridDesc)
+    sig = {
+        "ac_workspace_bytes": [dp, ctypes.POINTER(ctypes.c_size_t)],
+        "ac_create": [dp, vp, vp, vp, ctypes.POINTER(vp)],
+        "ac_step": [vp, i64],
+        "ac_energy": [vp, ctypes.POINTER(dbl)],
+        "ac_phase_volume": [vp, ctypes.POINTER(dbl)],
+        "ac_observe": [vp, ctypes.POINTER(dbl)],
+        "ac_init_sphere": [vp, dbl, dbl, dbl, dbl, dbl, dbl, dbl],
+        "ac_init_random": [vp, u64, dbl],
+        "ac_set_schedule": [vp, i32, i32],
+        "ac_get_schedule": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "ac_autotune": [vp, i64],
+        "ac_set_graph": [vp, i32],
+        "ac_status": [vp],
+        "ac_launch_count": [vp, ctypes.POINTER(i64)],
+        "ac_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ac_last_error.argtypes = []
+    L.ac_last_error.restype = ctypes.c_char_p
+    L.ac_version.argtypes = []
+    L.ac_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().ac_last_error().decode()
+
+
+def check(rc: int) -> int:
+    if rc != AC_OK:
+        raise AcError(rc, last_error())
+    return rc
+
+
+# ------------------------------------------------------------ entry points --
+
+def make_desc(ndim: int, dtype: int, nx: int, ny: int, nz: int, pitch_x: int,
+              h: float, eps: float, dt: float) -> AcGridDesc:
+    return AcGridDesc(ndim, dtype, nx, ny, nz, pitch_x, h, eps, dt)
+
+
+def ac_workspace_bytes(desc: AcGridDesc) -> int:
+    out = ctypes.c_size_t()
+    check(lib().ac_workspace_bytes(ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
+
+
+def ac_create(desc: AcGridDesc, phi_ptr: int, ws_ptr: int, stream_ptr: int) -> int:
+    h = ctypes.c_void_p()
+    check(lib().ac_create(ctypes.byref(desc), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(ws_ptr),
+                          ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def ac_step(ctx: int, n: int) -> None:
+    check(lib().ac_step(ctypes.c_void_p(ctx), int(n)))
+
+
+def ac_energy(ctx: int) -> float:
+    out = ctypes.c_double()
+    check(lib().ac_energy(ctypes.c_void_p(ctx), ctypes.byref(out)))
+    return out.value
+
+
+def ac_phase_volume(ctx: int) -> float:
+    out = ctypes.c_double()
+    check(lib().ac_phase_volume(ctypes.c_void_p(ctx), ctypes.byref(out)))
+    return out.value
+
+
+def ac_observe(ctx: int, allow_nonfinite: bool = False) -> tuple:
+    out = (ctypes.c_double * 3)()
+    rc = lib().ac_observe(ctypes.c_void_p(ctx), out)
+    if not (allow_nonfinite and rc == AC_ERR_NONFINITE):
+        check(rc)
+    return out[0], out[1], out[2]
+
+
+def ac_init_sphere(ctx: int, lower=(0.0, 0.0, 0.0), center=(0.5, 0.5, 0.5), r0: float = 0.25) -> None:
+    check(lib().ac_init_sphere(ctypes.c_void_p(ctx), *map(float, lower), *map(float, center), float(r0)))
+
+
+def ac_init_random(ctx: int, seed: int, amplitude: float = 0.1) -> None:
+    check(lib().ac_init_random(ctypes.c_void_p(ctx), int(seed), float(amplitude)))
+
+
+def ac_set_schedule(ctx: int, variant: int, k: int) -> None:
+    check(lib().ac_set_schedule(ctypes.c_void_p(ctx), int(variant), int(k)))
+
+
+def ac_get_schedule(ctx: int) -> tuple:
+    v, k = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().ac_get_schedule(ctypes.c_void_p(ctx), ctypes.byref(v), ctypes.byref(k)))
+    return v.value, k.value
+
+
+def ac_autotune(ctx: int, steps_per_trial: int = 64) -> None:
+    check(lib().ac_autotune(ctypes.c_void_p(ctx), int(steps_per_trial)))
+
+
+def ac_set_graph(ctx: int, enable: bool) -> None:
+    check(lib().ac_set_graph(ctypes.c_void_p(ctx), int(bool(enable))))
+
+
+def ac_status(ctx: int) -> int:
+    return lib().ac_status(ctypes.c_void_p(ctx))
+
+
+def ac_launch_count(ctx: int) -> int:
+    out = ctypes.c_int64()
+    check(lib().ac_launch_count(ctypes.c_void_p(ctx), ctypes.byref(out)))
+    return out.value
+
+
+def ac_destroy(ctx: int) -> None:
+    check(lib().ac_destroy(ctypes.c_void_p(ctx)))
+
+
+def ac_version() -> str:
+    return lib().ac_version().decode()

@@ -1,0 +1,537 @@
+// C ABI of the Allen-Cahn stepper: validation, contexts, launch planning,
+// reductions, initial conditions, autotuning and CUDA-graph replay.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace ac;
+
+// ---------------------------------------------------------------- errors --
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define AC_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(AC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+  } while (0)
+
+// ----------------------------------------------------------- tensor maps --
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+static size_t elem_size(int dtype) { return dtype == AC_F64 ? 8 : dtype == AC_F32 ? 4 : 2; }
+
+static CUtensorMapDataType tmap_type(int dtype) {
+  return dtype == AC_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+         : dtype == AC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+}
+
+// ---------------------------------------------------------------- context --
+struct MapPair {
+  bool valid = false;
+  CUtensorMap phi, ws;
+};
+
+struct ac_ctx {
+  ac_grid_desc d;
+  void *phi = nullptr, *ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  GridParams gp;
+  int *d_status = nullptr;
+  double *d_partials = nullptr, *d_out = nullptr, *h_out = nullptr;
+  int variant = AC_VARIANT_AUTO, k = 0;  // user request
+  int tuned_variant = 0, tuned_k = 0;    // autotuner result (0 = none)
+  MapPair maps[AC_MAX_K + 1];
+  // graph replay
+  bool use_graph = false;
+  int64_t graph_n = -1;
+  int graph_variant = -1, graph_k = -1;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;  // kernels in the captured graph
+  // kernels this context has put on its stream (graph replays count their nodes)
+  int64_t launches = 0;
+};
+
+static int validate_desc(const ac_grid_desc *d) {
+  if (!d) return fail(AC_ERR_INVALID, "descriptor is NULL");
+  if (d->ndim != 2 && d->ndim != 3) return fail(AC_ERR_INVALID, "ndim must be 2 or 3 (got %d)", d->ndim);
+  if (d->dtype != AC_F64 && d->dtype != AC_F32 && d->dtype != AC_F16S)
+    return fail(AC_ERR_INVALID, "unknown dtype %d", d->dtype);
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+    return fail(AC_ERR_INVALID, "grid sizes must be >= 1 (got %lld x %lld x %lld)",
+                (long long)d->nx, (long long)d->ny, (long long)d->nz);
+  if (d->ndim == 2 && d->nz != 1) return fail(AC_ERR_INVALID, "2D grids need nz == 1");
+  const int64_t lim = (int64_t)1 << 30;
+  if (d->nx >= lim || d->ny >= lim || d->nz >= lim || d->pitch_x >= lim)
+    return fail(AC_ERR_INVALID, "grid extent too large (each axis and pitch < 2^30)");
+  if (d->pitch_x < d->nx) return fail(AC_ERR_INVALID, "pitch_x < nx");
+  if ((d->pitch_x * (int64_t)elem_size(d->dtype)) % 16 != 0)
+    return fail(AC_ERR_INVALID, "pitch_x * element size must be a multiple of 16 bytes");
+  if (!(std::isfinite(d->h) && d->h > 0) || !(std::isfinite(d->eps) && d->eps > 0) ||
+      !(std::isfinite(d->dt) && d->dt > 0))
+    return fail(AC_ERR_INVALID, "h, eps and dt must be finite and > 0");
+  const double lap_limit = d->h * d->h / (2.0 * d->ndim);
+  if (d->dt > lap_limit * (1.0 + 1e-12))
+    return fail(AC_ERR_INVALID, "dt = %g exceeds the explicit stability limit h^2/(2 ndim) = %g",
+                d->dt, lap_limit);
+  if (d->dt > d->eps * d->eps * (1.0 + 1e-12))
+    return fail(AC_ERR_INVALID, "dt = %g exceeds eps^2 = %g (reaction step alpha > 1)", d->dt,
+                d->eps * d->eps);
+  return AC_OK;
+}
+
+static size_t field_bytes(const ac_grid_desc *d) {
+  return (size_t)d->pitch_x * (size_t)d->ny * (size_t)d->nz * elem_size(d->dtype);
+}
+
+extern "C" int ac_workspace_bytes(const ac_grid_desc *desc, size_t *out) {
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (!out) return fail(AC_ERR_INVALID, "out is NULL");
+  *out = field_bytes(desc);
+  return AC_OK;
+}
+
+static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(AC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  const ac_grid_desc &d = c->d;
+  const size_t es = elem_size(d.dtype);
+  cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)(d.pitch_x * es), (cuuint64_t)(d.pitch_x * d.ny * es)};
+  cuuint32_t box[3], estr[3] = {1, 1, 1};
+  cuuint32_t rank;
+  if (kind == 2) {
+    Stream2DGeom gm = stream2d_geom(d.dtype, k);
+    box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
+    rank = 2;
+  } else {
+    Stream3DGeom gm = stream3d_geom(d.dtype, k);
+    box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
+    rank = 3;
+  }
+  CUresult r = fn(out, tmap_type(d.dtype), rank, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(AC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return AC_OK;
+}
+
+static int ensure_maps(ac_ctx *c, int k) {
+  MapPair &m = c->maps[k];
+  if (m.valid) return AC_OK;
+  const int kind = c->d.ndim;
+  int rc = encode_map(c, c->phi, kind, k, &m.phi);
+  if (rc) return rc;
+  rc = encode_map(c, c->ws, kind, k, &m.ws);
+  if (rc) return rc;
+  m.valid = true;
+  return AC_OK;
+}
+
+static void release_graph(ac_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_n = -1;
+}
+
+extern "C" int ac_create(const ac_grid_desc *desc, void *phi_dev, void *workspace_dev,
+                         void *cuda_stream, ac_ctx **out) {
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (!out) return fail(AC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!phi_dev || !workspace_dev) return fail(AC_ERR_INVALID, "phi and workspace must be non-NULL");
+  if (((uintptr_t)phi_dev | (uintptr_t)workspace_dev) & 15)
+    return fail(AC_ERR_INVALID, "phi and workspace must be 16-byte aligned");
+  const size_t bytes = field_bytes(desc);
+  const uintptr_t a = (uintptr_t)phi_dev, b = (uintptr_t)workspace_dev;
+  if (a < b + bytes && b < a + bytes) return fail(AC_ERR_INVALID, "phi and workspace overlap");
+  cudaPointerAttributes pa{}, pb{};
+  if (cudaPointerGetAttributes(&pa, phi_dev) != cudaSuccess ||
+      cudaPointerGetAttributes(&pb, workspace_dev) != cudaSuccess ||
+      (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+      (pb.type != cudaMemoryTypeDevice && pb.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    return fail(AC_ERR_INVALID, "phi and workspace must be CUDA device memory");
+  }
+  ac_ctx *c = new (std::nothrow) ac_ctx();
+  if (!c) return fail(AC_ERR_NOMEM, "out of host memory");
+  c->d = *desc;
+  c->phi = phi_dev;
+  c->ws = workspace_dev;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->gp.nx = desc->nx;
+  c->gp.ny = desc->ny;
+  c->gp.nz = desc->nz;
+  c->gp.pitch = desc->pitch_x;
+  c->gp.alpha = desc->dt / (desc->eps * desc->eps);
+  c->gp.beta = desc->dt / (desc->h * desc->h);
+  cudaError_t e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * 4 * kReduceBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_out, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_status); cudaFree(c->d_partials); cudaFree(c->d_out); cudaFreeHost(c->h_out);
+    delete c;
+    cudaGetLastError();
+    return fail(AC_ERR_NOMEM, "internal allocation failed: %s", cudaGetErrorString(e));
+  }
+  c->gp.status = c->d_status;
+  *out = c;
+  return AC_OK;
+}
+
+extern "C" int ac_destroy(ac_ctx *c) {
+  if (!c) return AC_OK;
+  cudaStreamSynchronize(c->stream);
+  release_graph(c);
+  cudaFree(c->d_status);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_out);
+  cudaFreeHost(c->h_out);
+  delete c;
+  return AC_OK;
+}
+
+// ------------------------------------------------------------- schedules --
+static bool schedule_ok(const ac_ctx *c, int variant, int k) {
+  if (variant == AC_VARIANT_DIRECT) return k == 1;
+  if (variant == AC_VARIANT_STREAM)
+    return c->d.ndim == 2 ? stream2d_supported(c->d.dtype, k) : stream3d_supported(c->d.dtype, k);
+  return false;
+}
+
+static void default_schedule(const ac_ctx *c, int *variant, int *k) {
+  *variant = AC_VARIANT_STREAM;
+  if (c->d.ndim == 2) *k = c->d.dtype == AC_F64 ? 2 : 4;
+  else *k = 2;
+  if (!schedule_ok(c, *variant, *k)) *k = 1;
+}
+
+static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
+  if (c->variant != AC_VARIANT_AUTO) { *variant = c->variant; *k = c->k; return; }
+  if (c->tuned_variant) { *variant = c->tuned_variant; *k = c->tuned_k; return; }
+  default_schedule(c, variant, k);
+}
+
+extern "C" int ac_set_schedule(ac_ctx *c, int32_t variant, int32_t k) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (variant == AC_VARIANT_AUTO && k == 0) {
+    c->variant = AC_VARIANT_AUTO;
+    c->k = 0;
+    return AC_OK;
+  }
+  if (k < 1 || k > AC_MAX_K) return fail(AC_ERR_INVALID, "k must be in 1..%d", AC_MAX_K);
+  if (variant != AC_VARIANT_DIRECT && variant != AC_VARIANT_STREAM)
+    return fail(AC_ERR_INVALID, "unknown variant %d", variant);
+  if (!schedule_ok(c, variant, k))
+    return fail(AC_ERR_UNSUPPORTED, "variant %d with k = %d is not available for ndim %d dtype %d",
+                variant, k, c->d.ndim, c->d.dtype);
+  c->variant = variant;
+  c->k = k;
+  return AC_OK;
+}
+
+extern "C" int ac_get_schedule(ac_ctx *c, int32_t *variant, int32_t *k) {
+  if (!c || !variant || !k) return fail(AC_ERR_INVALID, "NULL argument");
+  int v, kk;
+  effective_schedule(c, &v, &kk);
+  *variant = v;
+  *k = kk;
+  return AC_OK;
+}
+
+// ------------------------------------------------------------- stepping ---
+// Depths of the launches for n steps at depth k: as many k as fit, then the
+// remainder; an odd launch count is made even by splitting a launch of
+// depth >= 2, so that the result lands back in phi.  Returns false if the
+// count stays odd (all depths 1): the caller then copies ws -> phi.
+static bool plan_depths(int64_t n, int k, std::vector<int> &depths) {
+  depths.clear();
+  for (int64_t i = 0; i < n / k; ++i) depths.push_back(k);
+  if (n % k) depths.push_back((int)(n % k));
+  if (depths.size() % 2 == 0) return true;
+  for (size_t i = depths.size(); i-- > 0;) {
+    if (depths[i] >= 2) {
+      const int a = depths[i] / 2, b = depths[i] - a;
+      depths[i] = b;
+      depths.insert(depths.begin() + i + 1, a);
+      return true;
+    }
+  }
+  return false;
+}
+
+static int issue_steps(ac_ctx *c, int64_t n, int variant, int k) {
+  std::vector<int> depths;
+  const bool even = variant == AC_VARIANT_DIRECT ? (n % 2 == 0) : plan_depths(n, k, depths);
+  if (variant == AC_VARIANT_DIRECT) depths.assign((size_t)n, 1);
+  bool src_is_phi = true;
+  for (int dep : depths) {
+    void *src = src_is_phi ? c->phi : c->ws;
+    void *dst = src_is_phi ? c->ws : c->phi;
+    cudaError_t e;
+    if (variant == AC_VARIANT_DIRECT) {
+      e = launch_direct(c->d.ndim, c->d.dtype, c->gp, src, dst, c->stream);
+    } else {
+      int rc = ensure_maps(c, dep);
+      if (rc) return rc;
+      const CUtensorMap *m = src_is_phi ? &c->maps[dep].phi : &c->maps[dep].ws;
+      e = c->d.ndim == 2 ? launch_stream2d(c->d.dtype, dep, c->gp, m, dst, c->num_sms, c->stream)
+                         : launch_stream3d(c->d.dtype, dep, c->gp, m, dst, c->num_sms, c->stream);
+    }
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stencil launch failed: %s", cudaGetErrorString(e));
+    ++c->launches;
+    src_is_phi = !src_is_phi;
+  }
+  if (!even) {
+    const size_t es = elem_size(c->d.dtype);
+    AC_CUDA(cudaMemcpy2DAsync(c->phi, c->d.pitch_x * es, c->ws, c->d.pitch_x * es, c->d.nx * es,
+                              (size_t)(c->d.ny * c->d.nz), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return AC_OK;
+}
+
+extern "C" int ac_step(ac_ctx *c, int64_t n) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (n < 0) return fail(AC_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return AC_OK;
+  int variant, k;
+  effective_schedule(c, &variant, &k);
+  if (!c->use_graph || c->stream == nullptr) return issue_steps(c, n, variant, k);
+  // graph replay: capture the launch sequence for this (n, schedule) once
+  if (c->graph_exec == nullptr || c->graph_n != n || c->graph_variant != variant ||
+      c->graph_k != k) {
+    release_graph(c);
+    AC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    const int64_t before = c->launches;
+    int rc = issue_steps(c, n, variant, k);
+    c->graph_launches = c->launches - before;
+    c->launches = before;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { c->graph_exec = nullptr; return fail(AC_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
+    c->graph_n = n;
+    c->graph_variant = variant;
+    c->graph_k = k;
+  }
+  AC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+  c->launches += c->graph_launches;
+  return AC_OK;
+}
+
+// ----------------------------------------------------------- reductions ---
+static int observe(ac_ctx *c, double out[4]) {
+  cudaError_t e = launch_observe(c->d.dtype, c->gp, c->phi, c->d_partials, c->d_out, c->stream);
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(e));
+  c->launches += 2;
+  AC_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  AC_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(out, c->h_out, 4 * sizeof(double));
+  return AC_OK;
+}
+
+static double cell_measure(const ac_ctx *c) {
+  return c->d.ndim == 3 ? c->d.h * c->d.h * c->d.h : c->d.h * c->d.h;
+}
+
+extern "C" int ac_observe(ac_ctx *c, double res[3]) {
+  if (!c || !res) return fail(AC_ERR_INVALID, "NULL argument");
+  double s[4];
+  int rc = observe(c, s);
+  if (rc) return rc;
+  const double hd = cell_measure(c);
+  res[0] = hd * (s[0] / (c->d.eps * c->d.eps) + 0.5 * s[1] / (c->d.h * c->d.h));
+  res[1] = hd * s[2];
+  res[2] = s[3];
+  if (s[3] > 0) return fail(AC_ERR_NONFINITE, "phi holds %.0f non-finite values", s[3]);
+  return AC_OK;
+}
+
+extern "C" int ac_energy(ac_ctx *c, double *out) {
+  if (!out) return fail(AC_ERR_INVALID, "out is NULL");
+  double r[3];
+  int rc = ac_observe(c, r);
+  if (rc && rc != AC_ERR_NONFINITE) return rc;
+  *out = r[0];
+  return rc;
+}
+
+extern "C" int ac_phase_volume(ac_ctx *c, double *out) {
+  if (!out) return fail(AC_ERR_INVALID, "out is NULL");
+  double r[3];
+  int rc = ac_observe(c, r);
+  if (rc && rc != AC_ERR_NONFINITE) return rc;
+  *out = r[1];
+  return rc;
+}
+
+extern "C" int ac_status(ac_ctx *c) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  int h = 0;
+  AC_CUDA(cudaStreamSynchronize(c->stream));
+  AC_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    AC_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
+    return fail(AC_ERR_TIMEOUT, "a bounded device wait expired (status %d)", h);
+  }
+  return AC_OK;
+}
+
+// ---------------------------------------------------- initial conditions --
+extern "C" int ac_init_sphere(ac_ctx *c, double lx, double ly, double lz, double cx, double cy,
+                              double cz, double r0) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (!std::isfinite(r0)) return fail(AC_ERR_INVALID, "r0 must be finite");
+  const double lo[3] = {lx, ly, lz}, ce[3] = {cx, cy, cz};
+  cudaError_t e = launch_init_sphere(c->d.dtype, c->gp, c->phi, c->d.h, lo, ce, r0, c->d.eps, c->stream);
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
+  ++c->launches;
+  return AC_OK;
+}
+
+extern "C" int ac_init_random(ac_ctx *c, uint64_t seed, double amplitude) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (!std::isfinite(amplitude)) return fail(AC_ERR_INVALID, "amplitude must be finite");
+  cudaError_t e = launch_init_random(c->d.dtype, c->gp, c->phi, seed, amplitude, c->stream);
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
+  ++c->launches;
+  return AC_OK;
+}
+
+// -------------------------------------------------------------- autotune --
+namespace {
+struct TuneKey {
+  int ndim, dtype, cls, device;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(ndim, dtype, cls, device) < std::tie(o.ndim, o.dtype, o.cls, o.device);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+static int size_class(const ac_grid_desc &d) {
+  const double cells = (double)d.nx * (double)d.ny * (double)d.nz;
+  return (int)std::floor(std::log2(std::max(1.0, cells)));
+}
+
+extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (steps_per_trial < 1) return fail(AC_ERR_INVALID, "steps_per_trial must be >= 1");
+  const TuneKey key{c->d.ndim, c->d.dtype, size_class(c->d), c->device};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c->tuned_variant = it->second.first;
+      c->tuned_k = it->second.second;
+      return AC_OK;
+    }
+  }
+  // candidates: the direct kernel and every streaming depth
+  std::vector<std::pair<int, int>> cand;
+  cand.push_back({AC_VARIANT_DIRECT, 1});
+  for (int k = 1; k <= AC_MAX_K; ++k)
+    if (schedule_ok(c, AC_VARIANT_STREAM, k)) cand.push_back({AC_VARIANT_STREAM, k});
+  const size_t bytes = field_bytes(&c->d);
+  void *backup = nullptr;
+  AC_CUDA(cudaMalloc(&backup, bytes));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = AC_OK;
+  float best = 1e30f;
+  std::pair<int, int> best_c = cand.front();
+  cudaMemcpyAsync(backup, c->phi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  for (auto &cd : cand) {
+    // steps rounded to a multiple of 2k so every candidate runs full passes
+    const int64_t n = std::max<int64_t>(2 * cd.second, steps_per_trial / (2 * cd.second) * (2 * cd.second));
+    rc = issue_steps(c, 2 * cd.second, cd.first, cd.second);  // warm-up
+    if (rc) break;
+    cudaEventRecord(e0, c->stream);
+    rc = issue_steps(c, n, cd.first, cd.second);
+    if (rc) break;
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const float per_step = ms / (float)n;
+    if (per_step < best) { best = per_step; best_c = cd; }
+    cudaMemcpyAsync(c->phi, backup, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(backup);
+  if (rc) return rc;
+  c->tuned_variant = best_c.first;
+  c->tuned_k = best_c.second;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best_c;
+  return AC_OK;
+}
+
+extern "C" int ac_set_graph(ac_ctx *c, int32_t enable) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (enable && c->stream == nullptr)
+    return fail(AC_ERR_UNSUPPORTED, "graph replay needs a non-default stream");
+  c->use_graph = enable != 0;
+  if (!c->use_graph) release_graph(c);
+  return AC_OK;
+}
+
+extern "C" int ac_launch_count(ac_ctx *c, int64_t *out) {
+  if (!c || !out) return fail(AC_ERR_INVALID, "NULL argument");
+  *out = c->launches;
+  return AC_OK;
+}
+
+extern "C" const char *ac_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *ac_version(void) { return "1.0.0 sm_103a"; }

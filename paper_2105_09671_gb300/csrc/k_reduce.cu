@@ -1,0 +1,98 @@
+// FP64 reductions over the field: the discrete Ginzburg-Landau energy terms,
+// the phase volume and a non-finite sentinel, in one pass.
+//
+//   bulk = sum_cells F(phi),  F(phi) = (phi^2 - 1)^2 / 4       (Section 1)
+//   grad = sum_{interior faces (a, b)} (phi_a - phi_b)^2
+//   vol  = sum_cells (1 + phi) / 2
+//
+// The host turns these into E_h = h^d (bulk / eps^2 + grad / (2 h^2)) and
+// V = h^d vol.  Every term is formed and accumulated in FP64 (sums over
+// 1e8 cells need it).  The result is deterministic: a fixed grid of blocks
+// each reduces a fixed set of rows in a fixed order, and a single block adds
+// the per-block partials in index order.
+#include "kernels.h"
+
+namespace ac {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) observe_partial(const T *__restrict__ phi, GridParams g,
+                                                       double *__restrict__ partials) {
+  constexpr int kWarps = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double bulk = 0.0, grad = 0.0, vol = 0.0, bad = 0.0;
+  const int64_t rows = g.ny * g.nz;
+  const int64_t plane = g.pitch * g.ny;
+  // each warp takes whole rows, rows strided over all warps of the grid
+  for (int64_t r = (int64_t)blockIdx.x * kWarps + warp; r < rows;
+       r += (int64_t)gridDim.x * kWarps) {
+    const int64_t j = r % g.ny, k = r / g.ny;
+    const T *row = phi + k * plane + j * g.pitch;
+    const bool has_up = j + 1 < g.ny, has_front = k + 1 < g.nz;
+    for (int64_t i = lane; i < g.nx; i += 32) {
+      const double p = (double)to_c(row[i]);
+      if (!isfinite(p)) bad += 1.0;
+      const double q = p * p - 1.0;
+      bulk += 0.25 * q * q;
+      vol += 0.5 * (1.0 + p);
+      if (i + 1 < g.nx) { double d = (double)to_c(row[i + 1]) - p; grad += d * d; }
+      if (has_up) { double d = (double)to_c(row[i + g.pitch]) - p; grad += d * d; }
+      if (has_front) { double d = (double)to_c(row[i + plane]) - p; grad += d * d; }
+    }
+  }
+  __shared__ double red[4][kWarps];
+  bulk = warp_sum(bulk); grad = warp_sum(grad); vol = warp_sum(vol); bad = warp_sum(bad);
+  if (lane == 0) { red[0][warp] = bulk; red[1][warp] = grad; red[2][warp] = vol; red[3][warp] = bad; }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
+    partials[(int64_t)blockIdx.x * 4 + threadIdx.x] = s;
+  }
+}
+
+// One block of 128 threads: thread t adds partials t, t+128, ... in order,
+// then a fixed tree over the 128 thread sums.
+__global__ void __launch_bounds__(128) observe_final(const double *__restrict__ partials, int nb,
+                                                     double *__restrict__ out) {
+  __shared__ double s[4][128];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += 128)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] += partials[(int64_t)b * 4 + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+template <typename T>
+static cudaError_t observe_t(const GridParams &g, const void *phi, double *partials, double *out,
+                             cudaStream_t s) {
+  observe_partial<T><<<kReduceBlocks, 256, 0, s>>>((const T *)phi, g, partials);
+  observe_final<<<1, 128, 0, s>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observe(int dtype, const GridParams &g, const void *phi, double *partials,
+                           double *out, cudaStream_t s) {
+  switch (dtype) {
+    case AC_F64: return observe_t<double>(g, phi, partials, out, s);
+    case AC_F32: return observe_t<float>(g, phi, partials, out, s);
+    case AC_F16S: return observe_t<__half>(g, phi, partials, out, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ac

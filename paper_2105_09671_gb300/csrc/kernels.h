@@ -1,0 +1,51 @@
+// Host-side launchers of the CUDA kernels (called by the C-ABI layer).
+#pragma once
+
+#include "common.cuh"
+
+namespace ac {
+
+// Geometry of the 2D streaming kernel for a storage type and depth k.
+struct Stream2DGeom {
+  int box_x, box_y;   // TMA box (elements, rows)
+  int halo_x;         // halo columns on each side (multiple of the vector width)
+  int out_w;          // output columns per warp strip
+};
+// Geometry of the 3D streaming kernel.
+struct Stream3DGeom {
+  int box_x, box_y;   // TMA box per plane (elements, rows)
+  int halo_x;         // halo columns per side
+  int out_x, out_y;   // output tile
+  int threads;
+  int smem_bytes;
+};
+
+bool stream2d_supported(int dtype, int k);
+Stream2DGeom stream2d_geom(int dtype, int k);
+bool stream3d_supported(int dtype, int k);
+Stream3DGeom stream3d_geom(int dtype, int k);
+
+// One step per launch, clamped global-memory neighbours (2D and 3D).
+cudaError_t launch_direct(int ndim, int dtype, const GridParams &g, const void *src, void *dst,
+                          cudaStream_t s);
+// k steps per launch.  src_map describes the source field with the box of
+// stream{2,3}d_geom(dtype, k).
+cudaError_t launch_stream2d(int dtype, int k, const GridParams &g, const CUtensorMap *src_map,
+                            void *dst, int num_sms, cudaStream_t s);
+cudaError_t launch_stream3d(int dtype, int k, const GridParams &g, const CUtensorMap *src_map,
+                            void *dst, int num_sms, cudaStream_t s);
+
+// FP64 reductions: out[0] = sum F(phi), out[1] = sum over interior faces of
+// (phi_a - phi_b)^2, out[2] = sum (1 + phi)/2, out[3] = non-finite count.
+// partials must hold kReduceBlocks * 4 doubles.
+constexpr int kReduceBlocks = 1216;
+cudaError_t launch_observe(int dtype, const GridParams &g, const void *phi, double *partials,
+                           double *out, cudaStream_t s);
+
+cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double h,
+                               const double lower[3], const double center[3], double r0,
+                               double eps, cudaStream_t s);
+cudaError_t launch_init_random(int dtype, const GridParams &g, void *phi, uint64_t seed,
+                               double amplitude, cudaStream_t s);
+
+}  // namespace ac

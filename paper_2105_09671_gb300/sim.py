@@ -1,0 +1,135 @@
+"""PyTorch-facing handle for one Allen-Cahn grid.
+
+PyTorch provides the device memory (the field and its ping-pong workspace)
+and the CUDA stream; every step, reduction and initial condition runs in
+``libac.so`` through the C ABI.  Nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_TORCH = {L.AC_F64: torch.float64, L.AC_F32: torch.float32, L.AC_F16S: torch.float16}
+_NUMPY = {L.AC_F64: np.float64, L.AC_F32: np.float32, L.AC_F16S: np.float16}
+DTYPES = {"f64": L.AC_F64, "f32": L.AC_F32, "f16s": L.AC_F16S}
+
+
+def _dtype_code(dtype) -> int:
+    if isinstance(dtype, str):
+        return DTYPES[dtype]
+    return int(dtype)
+
+
+class Simulation:
+    """A grid of shape (ny, nx) or (nz, ny, nx) resident on a CUDA device.
+
+    ``pitch_x`` defaults to nx rounded up to 128 bytes.  ``stream`` is a
+    ``torch.cuda.Stream`` (default: the current stream); all library work is
+    ordered on it.
+    """
+
+    def __init__(self, shape, h: float, eps: float, dt: float, dtype="f32", device="cuda",
+                 stream: torch.cuda.Stream | None = None, pitch_x: int | None = None):
+        if not torch.cuda.is_available():
+            raise L.AcError(L.AC_ERR_UNSUPPORTED, "a CUDA device is required")
+        self.code = _dtype_code(dtype)
+        shape = tuple(int(s) for s in shape)
+        if len(shape) == 2:
+            self.nz, self.ny, self.nx = 1, shape[0], shape[1]
+            self.ndim = 2
+        elif len(shape) == 3:
+            self.nz, self.ny, self.nx = shape
+            self.ndim = 3
+        else:
+            raise ValueError("shape must have 2 or 3 entries")
+        self.shape = shape
+        es = np.dtype(_NUMPY[self.code]).itemsize
+        per = 128 // es
+        self.pitch_x = int(pitch_x) if pitch_x is not None else -(-self.nx // per) * per
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h, self.eps, self.dt = float(h), float(eps), float(dt)
+        self.desc = L.make_desc(self.ndim, self.code, self.nx, self.ny, self.nz, self.pitch_x,
+                                self.h, self.eps, self.dt)
+        nbytes = L.ac_workspace_bytes(self.desc)
+        n = nbytes // es
+        tdt = _TORCH[self.code]
+        with torch.cuda.device(self.device):
+            self._buf = torch.zeros(n, dtype=tdt, device=self.device)
+            self._ws = torch.zeros(n, dtype=tdt, device=self.device)
+            self.ctx = L.ac_create(self.desc, self._buf.data_ptr(), self._ws.data_ptr(),
+                                   self.stream.cuda_stream)
+
+    # -- field access (views of the caller-owned buffer) ---------------------
+    @property
+    def phi(self) -> torch.Tensor:
+        """The field as a strided view, shape ``self.shape``."""
+        v = self._buf.view(self.nz, self.ny, self.pitch_x)[:, :, : self.nx]
+        return v[0] if self.ndim == 2 else v
+
+    @property
+    def padded(self) -> torch.Tensor:
+        return self._buf.view(self.nz, self.ny, self.pitch_x)
+
+    def load(self, array) -> None:
+        """Copy a host array (any float dtype) into the field, rounding to the storage type."""
+        a = np.asarray(array)
+        if a.shape != self.shape:
+            raise ValueError(f"shape {a.shape} != {self.shape}")
+        t = torch.from_numpy(np.ascontiguousarray(a.astype(_NUMPY[self.code])))
+        with torch.cuda.stream(self.stream):
+            self.phi.copy_(t.to(self.device, non_blocking=False))
+
+    def to_numpy(self) -> np.ndarray:
+        self.stream.synchronize()
+        return self.phi.cpu().numpy().copy()
+
+    # -- the C ABI -------------------------------------------------------------
+    def step(self, n: int) -> None:
+        L.ac_step(self.ctx, n)
+
+    def energy(self) -> float:
+        return L.ac_energy(self.ctx)
+
+    def phase_volume(self) -> float:
+        return L.ac_phase_volume(self.ctx)
+
+    def observe(self, allow_nonfinite: bool = False):
+        return L.ac_observe(self.ctx, allow_nonfinite)
+
+    def init_sphere(self, r0: float = 0.25, center=(0.5, 0.5, 0.5), lower=(0.0, 0.0, 0.0)) -> None:
+        L.ac_init_sphere(self.ctx, lower, center, r0)
+
+    def init_random(self, seed: int, amplitude: float = 0.1) -> None:
+        L.ac_init_random(self.ctx, seed, amplitude)
+
+    def set_schedule(self, variant: int, k: int) -> None:
+        L.ac_set_schedule(self.ctx, variant, k)
+
+    def schedule(self):
+        return L.ac_get_schedule(self.ctx)
+
+    def autotune(self, steps_per_trial: int = 64) -> None:
+        L.ac_autotune(self.ctx, steps_per_trial)
+
+    def set_graph(self, enable: bool) -> None:
+        L.ac_set_graph(self.ctx, enable)
+
+    def launch_count(self) -> int:
+        return L.ac_launch_count(self.ctx)
+
+    def status(self) -> int:
+        return L.ac_status(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            L.ac_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

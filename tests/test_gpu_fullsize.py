@@ -1,0 +1,104 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (the default schedule of ac_step).
+
+The oracle cannot step 512^3 in seconds, but after n steps a cell depends
+only on the cells within n of it (domain of dependence).  For each sampled
+cell the oracle steps the block of +-(n+1) cells around it, cut at the domain
+faces (where the block keeps the true zero-Neumann boundary), and the centre
+value is compared.  Samples include every corner, domain edges and the
+tile / chunk seams of the CUDA kernels.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_09671_gb300 as ac
+from paper_2105_09671_gb300 import workloads as wl
+
+from gpu_util import TOL_MAXABS
+
+pytestmark = pytest.mark.gpu
+
+
+def _seam_coords(n, tile, halo_steps):
+    cs = {0, 1, n - 2, n - 1, n // 2}
+    for t in range(tile, n, tile):
+        cs.update({t - 1, t, t + 1})
+    return sorted(c for c in cs if 0 <= c < n)
+
+
+def _samples(shape, rng, seams, count):
+    pts = set()
+    for corner in itertools.product(*[(0, s - 1) for s in shape]):
+        pts.add(corner)
+    axes = [seams[i] for i in range(len(shape))]
+    for _ in range(count):
+        pts.add(tuple(int(rng.choice(a)) for a in axes))
+        pts.add(tuple(int(rng.integers(0, s)) for s in shape))
+    return sorted(pts)
+
+
+def _check_samples(phi0, out, h, eps, dt, n, pts, tol):
+    worst = 0.0
+    for p in pts:
+        lo = [max(0, c - n - 1) for c in p]
+        hi = [min(s, c + n + 2) for c, s in zip(p, phi0.shape)]
+        block = phi0[tuple(slice(a, b) for a, b in zip(lo, hi))].astype(np.float64)
+        ref = oracle.step(block, h, eps, dt, n)
+        centre = tuple(c - a for c, a in zip(p, lo))
+        err = abs(float(out[p]) - float(ref[centre]))
+        worst = max(worst, err)
+        assert err <= tol, f"cell {p}: |gpu - oracle| = {err:.3e}"
+    return worst
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_separation_4096_sampled(dtype):
+    w = wl.SEPARATION_4096
+    sim = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype)
+    try:
+        sim.init_random(seed=w.seed, amplitude=0.1)
+        phi0 = sim.to_numpy()
+        v, k = sim.schedule()
+        n = 2 * k + 1
+        sim.step(n)
+        out = sim.to_numpy()
+    finally:
+        sim.close()
+    rng = np.random.default_rng(0)
+    seams = [_seam_coords(4096, 128, k), _seam_coords(4096, 120 if dtype == "f32" else 112, k)]
+    pts = _samples(w.shape, rng, seams, 150)
+    _check_samples(phi0, out, w.h, w.eps, w.dt, n, pts, TOL_MAXABS[dtype])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16s"])
+def test_sphere_512_sampled(dtype):
+    w = wl.SPHERE_512
+    sim = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype)
+    try:
+        sim.init_sphere(r0=w.r0)
+        phi0 = sim.to_numpy()
+        v, k = sim.schedule()
+        n = 2 * k + 1
+        e0 = sim.energy()
+        sim.step(n)
+        out = sim.to_numpy()
+        e1 = sim.energy()
+    finally:
+        sim.close()
+    rng = np.random.default_rng(1)
+    seams = [_seam_coords(512, 16, k), _seam_coords(512, 32, k), _seam_coords(512, 128, k)]
+    # a sphere is mostly +-1 far from its surface: bias samples towards the interface
+    pts = _samples(w.shape, rng, seams, 120)
+    c = (np.arange(512) + 0.5) / 512 - 0.5
+    for _ in range(120):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        r = w.r0 + rng.uniform(-3, 3) * w.eps
+        p = tuple(int(np.clip(np.searchsorted(c, r * d[i]), 0, 511)) for i in range(3))
+        pts.append(p[::-1])
+    tol = TOL_MAXABS["f32"] if dtype == "f32" else 2e-3  # one FP16 rounding per pass
+    _check_samples(phi0.astype(np.float64), out.astype(np.float64), w.h, w.eps, w.dt, n, pts, tol)
+    assert e1 < e0

@@ -170,7 +170,7 @@ def init_field(sim, w):
 
 
 # ------------------------------------------------------------ CPU oracle ---
-def oracle_sample(w, target_s: float, max_steps: int = 20):
+def oracle_sample(w, target_s: float, max_steps: int = 400):
     """Time the FP64 oracle on the same grid for a bounded number of steps."""
     import numpy as np
     import oracle

@@ -178,6 +178,35 @@ int ac_status(ac_ctx *ctx);
  * number of single-step passes is a copy, not a kernel, and is not counted. */
 int ac_launch_count(ac_ctx *ctx, int64_t *out);
 
+/* Allocation-free variant of ac_observe, for callers that cannot allocate
+ * device or host memory at the point of the call: code running under a
+ * memory budget owned by someone else (a framework's caching allocator, a
+ * serving process with a fixed pool), and latency-critical loops where the
+ * device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.
+ * It needs no context (ac_create allocates) and calls no cudaMalloc,
+ * cudaFree or allocating routine: the per-block partial sums go to a fixed
+ * 512 KiB array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart; it
+ * computes the same observables as ac_observe.
+ *
+ *   desc     the grid descriptor (validated as for ac_create).
+ *   phi_dev  the field in device memory (16-byte aligned), laid out as desc says.
+ *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream).
+ *   out_dev  caller-owned device memory for 3 doubles (8-byte aligned):
+ *            out_dev[0] = E_h, out_dev[1] = V, out_dev[2] = non-finite count.
+ *
+ * Asynchronous: nothing is copied to the host and the stream is not
+ * synchronised.  Grids with ny * nz above 1048576 rows (the fixed scratch
+ * holds 16384 blocks of 64 rows) are rejected with AC_ERR_INVALID and a
+ * message naming the limit.  The first call on each device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture on the device.  All calls on a device share the
+ * array: calls whose kernels overlap on the GPU (for example, issued on two
+ * streams without ordering between them) race and give wrong sums.  Each
+ * call writes every partial it reads, so no state carries over between calls. */
+int ac_observe_noalloc(const ac_grid_desc *desc, const void *phi_dev, void *cuda_stream,
+                       double *out_dev);
+
 /* Release the context's internal buffers.  Does not touch phi/workspace.
  * Synchronises the stream first.  NULL is accepted. */
 int ac_destroy(ac_ctx *ctx);

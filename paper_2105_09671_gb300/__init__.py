@@ -8,7 +8,7 @@ from ._lib import (AC_ERR_CUDA, AC_ERR_INVALID, AC_ERR_NOMEM, AC_ERR_NONFINITE, 
                    AC_ERR_TIMEOUT, AC_ERR_UNSUPPORTED, AC_F16S, AC_F32, AC_F64, AC_MAX_K, AC_OK,
                    AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM, AcError, AcGridDesc,
                    EXPORTED, ac_autotune, ac_create, ac_destroy, ac_energy, ac_get_schedule,
-                   ac_init_random, ac_init_sphere, ac_launch_count, ac_observe, ac_phase_volume, ac_set_graph,
+                   ac_init_random, ac_init_sphere, ac_launch_count, ac_observe, ac_observe_noalloc, ac_phase_volume, ac_set_graph,
                    ac_set_schedule, ac_status, ac_step, ac_version, ac_workspace_bytes, lib,
                    lib_path, make_desc)
 

@@ -27,7 +27,8 @@ AC_MAX_K = 8
 EXPORTED = (
     "ac_workspace_bytes", "ac_create", "ac_step", "ac_energy", "ac_phase_volume", "ac_observe",
     "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_autotune",
-    "ac_set_graph", "ac_status", "ac_launch_count", "ac_destroy", "ac_last_error", "ac_version",
+    "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
+    "ac_last_error", "ac_version",
 )
 
 
@@ -84,6 +85,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_set_graph": [vp, i32],
         "ac_status": [vp],
         "ac_launch_count": [vp, ctypes.POINTER(i64)],
+        "ac_observe_noalloc": [dp, vp, vp, vp],
         "ac_destroy": [vp],
     }
     for name, args in sig.items():
@@ -186,6 +188,13 @@ def ac_launch_count(ctx: int) -> int:
     out = ctypes.c_int64()
     check(lib().ac_launch_count(ctypes.c_void_p(ctx), ctypes.byref(out)))
     return out.value
+
+
+def ac_observe_noalloc(desc: AcGridDesc, phi_ptr: int, stream_ptr: int, out_ptr: int) -> None:
+    """Energy, volume and non-finite count of the field at phi_ptr into the
+    three device doubles at out_ptr, without any allocation (see include/ac.h)."""
+    check(lib().ac_observe_noalloc(ctypes.byref(desc), ctypes.c_void_p(phi_ptr),
+                                   ctypes.c_void_p(stream_ptr), ctypes.c_void_p(out_ptr)))
 
 
 def ac_destroy(ctx: int) -> None:

@@ -526,6 +526,39 @@ extern "C" int ac_set_graph(ac_ctx *c, int32_t enable) {
   return AC_OK;
 }
 
+// Allocation-free observation: no context, no cudaMalloc/cudaFree, no pinned
+// or pageable host buffers; the partial sums live in the library's fixed
+// module-global array (see k_reduce.cu) and the results in the caller's
+// device buffer.
+extern "C" int ac_observe_noalloc(const ac_grid_desc *desc, const void *phi_dev, void *cuda_stream,
+                                  double *out_dev) {
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (!phi_dev || !out_dev) return fail(AC_ERR_INVALID, "phi_dev and out_dev must be non-NULL");
+  if (((uintptr_t)phi_dev & 15) || ((uintptr_t)out_dev & 7))
+    return fail(AC_ERR_INVALID, "phi_dev must be 16-byte and out_dev 8-byte aligned");
+  const int64_t rows = desc->ny * desc->nz;
+  if (rows > observe_noalloc_max_rows())
+    return fail(AC_ERR_INVALID,
+                "ac_observe_noalloc: ny * nz = %lld rows exceeds the fixed scratch limit of %lld "
+                "rows (use ac_observe through a context instead)",
+                (long long)rows, (long long)observe_noalloc_max_rows());
+  GridParams g;
+  g.nx = desc->nx;
+  g.ny = desc->ny;
+  g.nz = desc->nz;
+  g.pitch = desc->pitch_x;
+  g.alpha = desc->dt / (desc->eps * desc->eps);
+  g.beta = desc->dt / (desc->h * desc->h);
+  g.status = nullptr;
+  const double hd = desc->ndim == 3 ? desc->h * desc->h * desc->h : desc->h * desc->h;
+  cudaError_t e = launch_observe_noalloc(desc->dtype, g, phi_dev, hd, desc->eps, desc->h, out_dev,
+                                         (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess)
+    return fail(AC_ERR_CUDA, "ac_observe_noalloc launch failed: %s", cudaGetErrorString(e));
+  return AC_OK;
+}
+
 extern "C" int ac_launch_count(ac_ctx *c, int64_t *out) {
   if (!c || !out) return fail(AC_ERR_INVALID, "NULL argument");
   *out = c->launches;

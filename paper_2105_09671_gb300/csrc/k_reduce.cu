@@ -10,6 +10,9 @@
 // 1e8 cells need it).  The result is deterministic: a fixed grid of blocks
 // each reduces a fixed set of rows in a fixed order, and a single block adds
 // the per-block partials in index order.
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace ac {
@@ -93,6 +96,89 @@ cudaError_t launch_observe(int dtype, const GridParams &g, const void *phi, doub
     case AC_F16S: return observe_t<__half>(g, phi, partials, out, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------- allocation-free variant --
+// ac_observe_noalloc (see include/ac.h) runs the same per-block partial-sum
+// kernel, but over a grid of one block per kNoAllocRowsPerBlock rows, with
+// its partial sums in the fixed array below instead of a buffer from
+// ac_create.  The array is a module global: every GPU that loads the library
+// holds its 512 KiB until the process exits, and all calls on a device share
+// it.  Each call writes every partial slot it later reads, so nothing in it
+// has to start at zero; two calls that overlap on the GPU (e.g. on different
+// streams) would overwrite each other's partials.
+
+constexpr int kNoAllocMaxBlocks = 16384;
+constexpr int kNoAllocRowsPerBlock = 64;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * 4];
+
+// Sums the partials in a fixed order (as observe_final) and forms the
+// observables on the device: out[0] = E_h, out[1] = V, out[2] = non-finite count.
+__global__ void __launch_bounds__(128) observe_final_noalloc(const double *__restrict__ partials,
+                                                             int nb, double hd, double inv_eps2,
+                                                             double half_inv_h2,
+                                                             double *__restrict__ out) {
+  __shared__ double s[4][128];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += 128)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] += partials[(int64_t)b * 4 + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = hd * (s[0][0] * inv_eps2 + s[1][0] * half_inv_h2);
+    out[1] = hd * s[2][0];
+    out[2] = s[3][0];
+  }
+}
+
+// Device address of g_noalloc_partials, looked up once per device (with that
+// device current) on the first call that uses it.
+static double *noalloc_scratch(int device, cudaError_t *err) {
+  static std::mutex mu;
+  static double *addr[64] = {nullptr};
+  std::lock_guard<std::mutex> lk(mu);
+  if (device < 0 || device >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  if (!addr[device]) {
+    void *p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (*err != cudaSuccess) return nullptr;
+    addr[device] = static_cast<double *>(p);
+  }
+  *err = cudaSuccess;
+  return addr[device];
+}
+
+int64_t observe_noalloc_max_rows() { return (int64_t)kNoAllocMaxBlocks * kNoAllocRowsPerBlock; }
+
+cudaError_t launch_observe_noalloc(int dtype, const GridParams &g, const void *phi, double hd,
+                                   double eps, double h, double *out_dev, cudaStream_t s) {
+  const int64_t rows = g.ny * g.nz;
+  if (rows > observe_noalloc_max_rows()) return cudaErrorInvalidValue;
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return e;
+  double *scratch = noalloc_scratch(device, &e);
+  if (!scratch) return e;
+  const int nb = (int)std::max<int64_t>(1, (rows + kNoAllocRowsPerBlock - 1) / kNoAllocRowsPerBlock);
+  switch (dtype) {
+    case AC_F64: observe_partial<double><<<nb, 256, 0, s>>>((const double *)phi, g, scratch); break;
+    case AC_F32: observe_partial<float><<<nb, 256, 0, s>>>((const float *)phi, g, scratch); break;
+    case AC_F16S: observe_partial<__half><<<nb, 256, 0, s>>>((const __half *)phi, g, scratch); break;
+    default: return cudaErrorInvalidValue;
+  }
+  observe_final_noalloc<<<1, 128, 0, s>>>(scratch, nb, hd, 1.0 / (eps * eps), 0.5 / (h * h), out_dev);
+  return cudaGetLastError();
 }
 
 }  // namespace ac

@@ -42,6 +42,13 @@ constexpr int kReduceBlocks = 1216;
 cudaError_t launch_observe(int dtype, const GridParams &g, const void *phi, double *partials,
                            double *out, cudaStream_t s);
 
+// Allocation-free variant of launch_observe: partial sums in a module-global
+// array (one block per 64 rows, at most observe_noalloc_max_rows() rows);
+// writes E_h, V and the non-finite count to out_dev[0..2] on the device.
+int64_t observe_noalloc_max_rows();
+cudaError_t launch_observe_noalloc(int dtype, const GridParams &g, const void *phi, double hd,
+                                   double eps, double h, double *out_dev, cudaStream_t s);
+
 cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double h,
                                const double lower[3], const double center[3], double r0,
                                double eps, cudaStream_t s);

@@ -156,9 +156,9 @@ def recorded_traffic(kernel: str, source: str):
 def workload(name: str):
     from paper_2105_09671_gb300 import workloads as wl
     if name == "sphere512":
-        return wl.SPHERE_512, "f32", "stream3d_k<float>", "k_stream3d.cu"
+        return wl.SPHERE_512, "f32", "stream3d_k<float>", "stream3d.cuh"
     if name == "separation4096":
-        return wl.SEPARATION_4096, "f32", "stream2d_k<float>", "k_stream2d.cu"
+        return wl.SEPARATION_4096, "f32", "stream2d_k<float>", "stream2d.cuh"
     raise SystemExit(f"unknown workload {name}")
 
 

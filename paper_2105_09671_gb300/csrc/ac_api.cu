@@ -243,9 +243,17 @@ static bool schedule_ok(const ac_ctx *c, int variant, int k) {
 }
 
 static void default_schedule(const ac_ctx *c, int *variant, int *k) {
+  // FP64 is bound by the GPU's FP64 rate, where the redundant halo work of
+  // temporal blocking costs more than the memory traffic it saves: one step
+  // per launch.  FP32 / FP16 storage are memory bound: stream with k > 1
+  // (measured best on GB300: 3D k = 2, 2D k = 4).
+  if (c->d.dtype == AC_F64) {
+    *variant = AC_VARIANT_DIRECT;
+    *k = 1;
+    return;
+  }
   *variant = AC_VARIANT_STREAM;
-  if (c->d.ndim == 2) *k = c->d.dtype == AC_F64 ? 2 : 4;
-  else *k = 2;
+  *k = c->d.ndim == 2 ? 4 : 2;
   if (!schedule_ok(c, *variant, *k)) *k = 1;
 }
 

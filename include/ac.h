@@ -178,6 +178,68 @@ int ac_status(ac_ctx *ctx);
  * number of single-step passes is a copy, not a kernel, and is not counted. */
 int ac_launch_count(ac_ctx *ctx, int64_t *out);
 
+/* ------------------------------------------------------ batched mode ---- */
+/* Many independent 2D grids (each its own size, eps, dt and state) advanced
+ * together by ONE persistent kernel launch (the paper runs one
+ * grid at a time).  Work items are the warp strips x row chunks of the 2D
+ * streaming stencil of every instance; a step-block of an item starts once
+ * its 3 x 3 neighbourhood has finished the previous one (bounded waits on
+ * per-item progress counters), so no grid-wide barrier is needed.  */
+typedef struct ac_batch ac_batch; /* opaque */
+
+/* Bytes of device workspace for count instances: the sum over instances of
+ * one field of the same layout, each rounded up to 256 bytes. */
+int ac_batch_workspace_bytes(const ac_grid_desc *descs, int32_t count, size_t *out);
+
+/* descs[i] / phi_devs[i]: instance i (ndim must be 2, all with one dtype;
+ * phi 16-byte aligned).  workspace_dev: 256-byte aligned, at least
+ * ac_batch_workspace_bytes() bytes, carved into one ping-pong partner per
+ * instance in index order.  The caller owns all buffers.  Allocates small
+ * internal tables (per-instance TMA descriptors, work items, progress
+ * counters, reduction buffers). */
+int ac_batch_create(const ac_grid_desc *descs, void *const *phi_devs, int32_t count,
+                    void *workspace_dev, void *cuda_stream, ac_batch **out);
+
+/* Advance instance i by n_per_instance[i] >= 0 steps of Eq. (pytorchACeq)
+ * (the same scheme and results as ac_step on that grid with the same depth
+ * k).  One kernel launch (plus a ws -> phi copy for an instance whose plan
+ * is an odd number of single steps).  Asynchronous; results in phi_devs.
+ * Re-planning (new n values or k) synchronises the stream once. */
+int ac_batch_step(ac_batch *batch, const int64_t *n_per_instance);
+
+/* Temporal-block depth k (1..4) of every instance; 0 = default (4 for
+ * FP32/FP16 storage, 1 for FP64). */
+int ac_batch_set_schedule(ac_batch *batch, int32_t k);
+int ac_batch_get_schedule(ac_batch *batch, int32_t *k);
+
+/* Time k = 1..4 on the batch's own fields (steps_per_trial steps each,
+ * fields saved to a temporary device buffer this call allocates and
+ * restored after each trial) and keep the fastest.  Synchronises. */
+int ac_batch_autotune(ac_batch *batch, int64_t steps_per_trial);
+
+/* Replay ac_batch_step through a CUDA graph (captured on the first call per
+ * plan; needs a non-default stream). */
+int ac_batch_set_graph(ac_batch *batch, int32_t enable);
+
+/* ac_observe for instance i (energy, volume, non-finite count).  Synchronises. */
+int ac_batch_observe(ac_batch *batch, int32_t i, double out[3]);
+
+/* Synchronises; AC_ERR_TIMEOUT if a bounded wait in the batched kernel
+ * expired since the last call (then the results are not valid). */
+int ac_batch_status(ac_batch *batch);
+
+/* Poll limit of each bounded wait in the batched kernel (0 = default,
+ * about a second).  Lowering it makes waits give up early; used to test
+ * the timeout path. */
+int ac_batch_set_wait_limit(ac_batch *batch, uint32_t polls);
+
+/* Kernels enqueued by this batch since creation (graph replays count the
+ * kernels they contain). */
+int ac_batch_launch_count(ac_batch *batch, int64_t *out);
+
+/* Release internal tables (not the caller's buffers).  Synchronises. */
+int ac_batch_destroy(ac_batch *batch);
+
 /* Allocation-free variant of ac_observe, for callers that cannot allocate
  * device or host memory at the point of the call: code running under a
  * memory budget owned by someone else (a framework's caching allocator, a

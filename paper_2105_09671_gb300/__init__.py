@@ -15,7 +15,7 @@ from ._lib import (AC_ERR_CUDA, AC_ERR_INVALID, AC_ERR_NOMEM, AC_ERR_NONFINITE, 
 
 def __getattr__(name):
     # torch is imported lazily so that the binding loads without it
-    if name in ("Simulation", "DTYPES"):
+    if name in ("Simulation", "Batch", "DTYPES"):
         from . import sim
         return getattr(sim, name)
     raise AttributeError(name)

@@ -29,6 +29,9 @@ EXPORTED = (
     "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_autotune",
     "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
     "ac_last_error", "ac_version",
+    "ac_batch_workspace_bytes", "ac_batch_create", "ac_batch_step", "ac_batch_set_schedule",
+    "ac_batch_get_schedule", "ac_batch_autotune", "ac_batch_set_graph", "ac_batch_observe",
+    "ac_batch_status", "ac_batch_set_wait_limit", "ac_batch_launch_count", "ac_batch_destroy",
 )
 
 
@@ -86,6 +89,18 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_status": [vp],
         "ac_launch_count": [vp, ctypes.POINTER(i64)],
         "ac_observe_noalloc": [dp, vp, vp, vp],
+        "ac_batch_workspace_bytes": [dp, i32, ctypes.POINTER(ctypes.c_size_t)],
+        "ac_batch_create": [dp, ctypes.POINTER(vp), i32, vp, vp, ctypes.POINTER(vp)],
+        "ac_batch_step": [vp, ctypes.POINTER(i64)],
+        "ac_batch_set_schedule": [vp, i32],
+        "ac_batch_get_schedule": [vp, ctypes.POINTER(i32)],
+        "ac_batch_autotune": [vp, i64],
+        "ac_batch_set_graph": [vp, i32],
+        "ac_batch_observe": [vp, i32, ctypes.POINTER(dbl)],
+        "ac_batch_status": [vp],
+        "ac_batch_set_wait_limit": [vp, ctypes.c_uint32],
+        "ac_batch_launch_count": [vp, ctypes.POINTER(i64)],
+        "ac_batch_destroy": [vp],
         "ac_destroy": [vp],
     }
     for name, args in sig.items():
@@ -203,3 +218,75 @@ def ac_destroy(ctx: int) -> None:
 
 def ac_version() -> str:
     return lib().ac_version().decode()
+
+
+# ------------------------------------------------------------- batched mode --
+
+def _desc_array(descs):
+    arr = (AcGridDesc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def ac_batch_workspace_bytes(descs) -> int:
+    out = ctypes.c_size_t()
+    check(lib().ac_batch_workspace_bytes(_desc_array(descs), len(descs), ctypes.byref(out)))
+    return out.value
+
+
+def ac_batch_create(descs, phi_ptrs, ws_ptr: int, stream_ptr: int) -> int:
+    h = ctypes.c_void_p()
+    ptrs = (ctypes.c_void_p * len(phi_ptrs))(*phi_ptrs)
+    check(lib().ac_batch_create(_desc_array(descs), ptrs, len(descs), ctypes.c_void_p(ws_ptr),
+                                ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def ac_batch_step(batch: int, n_per_instance) -> None:
+    arr = (ctypes.c_int64 * len(n_per_instance))(*[int(n) for n in n_per_instance])
+    check(lib().ac_batch_step(ctypes.c_void_p(batch), arr))
+
+
+def ac_batch_set_schedule(batch: int, k: int) -> None:
+    check(lib().ac_batch_set_schedule(ctypes.c_void_p(batch), int(k)))
+
+
+def ac_batch_get_schedule(batch: int) -> int:
+    k = ctypes.c_int32()
+    check(lib().ac_batch_get_schedule(ctypes.c_void_p(batch), ctypes.byref(k)))
+    return k.value
+
+
+def ac_batch_autotune(batch: int, steps_per_trial: int = 64) -> None:
+    check(lib().ac_batch_autotune(ctypes.c_void_p(batch), int(steps_per_trial)))
+
+
+def ac_batch_set_graph(batch: int, enable: bool) -> None:
+    check(lib().ac_batch_set_graph(ctypes.c_void_p(batch), int(bool(enable))))
+
+
+def ac_batch_observe(batch: int, i: int, allow_nonfinite: bool = False) -> tuple:
+    out = (ctypes.c_double * 3)()
+    rc = lib().ac_batch_observe(ctypes.c_void_p(batch), int(i), out)
+    if not (allow_nonfinite and rc == AC_ERR_NONFINITE):
+        check(rc)
+    return out[0], out[1], out[2]
+
+
+def ac_batch_status(batch: int) -> int:
+    return lib().ac_batch_status(ctypes.c_void_p(batch))
+
+
+def ac_batch_set_wait_limit(batch: int, polls: int) -> None:
+    check(lib().ac_batch_set_wait_limit(ctypes.c_void_p(batch), int(polls)))
+
+
+def ac_batch_launch_count(batch: int) -> int:
+    out = ctypes.c_int64()
+    check(lib().ac_batch_launch_count(ctypes.c_void_p(batch), ctypes.byref(out)))
+    return out.value
+
+
+def ac_batch_destroy(batch: int) -> None:
+    check(lib().ac_batch_destroy(ctypes.c_void_p(batch)))

@@ -21,6 +21,11 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libac.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Kernels use C++20 (templated lambdas for the unrolled streaming loops).
+# ac_batch.cu is host-only C++ that needs nothing newer than C++17, and
+# nvcc 13.0's front end aborts on it in C++20 mode (an internal assertion in
+# its standard-library destructor handling), so it is compiled as C++17.
+STD_OVERRIDE = {"ac_batch.cu": "-std=c++17"}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
 
@@ -50,7 +55,9 @@ def _stale() -> bool:
 
 def _compile(nvcc: str, src: str, verbose_ptxas: bool) -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    flags = [STD_OVERRIDE.get(os.path.basename(src), f) if f.startswith("-std=") else f
+             for f in NVCC_FLAGS]
+    cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -27,6 +27,13 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+namespace ac {
+int set_error(int code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace ac
+
 #define AC_CUDA(call)                                                                    \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
@@ -35,12 +42,8 @@ static int fail(int code, const char *fmt, ...) {
   } while (0)
 
 // ----------------------------------------------------------- tensor maps --
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-static EncodeTiledFn encode_fn() {
+EncodeTiledFn ac_encode_fn() {
   static EncodeTiledFn fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -54,9 +57,9 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static size_t elem_size(int dtype) { return dtype == AC_F64 ? 8 : dtype == AC_F32 ? 4 : 2; }
+size_t ac_elem_size(int dtype) { return dtype == AC_F64 ? 8 : dtype == AC_F32 ? 4 : 2; }
 
-static CUtensorMapDataType tmap_type(int dtype) {
+CUtensorMapDataType ac_tmap_type(int dtype) {
   return dtype == AC_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
          : dtype == AC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -89,7 +92,7 @@ struct ac_ctx {
   int64_t launches = 0;
 };
 
-static int validate_desc(const ac_grid_desc *d) {
+int ac_validate_desc(const ac_grid_desc *d) {
   if (!d) return fail(AC_ERR_INVALID, "descriptor is NULL");
   if (d->ndim != 2 && d->ndim != 3) return fail(AC_ERR_INVALID, "ndim must be 2 or 3 (got %d)", d->ndim);
   if (d->dtype != AC_F64 && d->dtype != AC_F32 && d->dtype != AC_F16S)
@@ -102,7 +105,7 @@ static int validate_desc(const ac_grid_desc *d) {
   if (d->nx >= lim || d->ny >= lim || d->nz >= lim || d->pitch_x >= lim)
     return fail(AC_ERR_INVALID, "grid extent too large (each axis and pitch < 2^30)");
   if (d->pitch_x < d->nx) return fail(AC_ERR_INVALID, "pitch_x < nx");
-  if ((d->pitch_x * (int64_t)elem_size(d->dtype)) % 16 != 0)
+  if ((d->pitch_x * (int64_t)ac_elem_size(d->dtype)) % 16 != 0)
     return fail(AC_ERR_INVALID, "pitch_x * element size must be a multiple of 16 bytes");
   if (!(std::isfinite(d->h) && d->h > 0) || !(std::isfinite(d->eps) && d->eps > 0) ||
       !(std::isfinite(d->dt) && d->dt > 0))
@@ -118,11 +121,11 @@ static int validate_desc(const ac_grid_desc *d) {
 }
 
 static size_t field_bytes(const ac_grid_desc *d) {
-  return (size_t)d->pitch_x * (size_t)d->ny * (size_t)d->nz * elem_size(d->dtype);
+  return (size_t)d->pitch_x * (size_t)d->ny * (size_t)d->nz * ac_elem_size(d->dtype);
 }
 
 extern "C" int ac_workspace_bytes(const ac_grid_desc *desc, size_t *out) {
-  int rc = validate_desc(desc);
+  int rc = ac_validate_desc(desc);
   if (rc) return rc;
   if (!out) return fail(AC_ERR_INVALID, "out is NULL");
   *out = field_bytes(desc);
@@ -130,10 +133,10 @@ extern "C" int ac_workspace_bytes(const ac_grid_desc *desc, size_t *out) {
 }
 
 static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) {
-  EncodeTiledFn fn = encode_fn();
+  EncodeTiledFn fn = ac_encode_fn();
   if (!fn) return fail(AC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
   const ac_grid_desc &d = c->d;
-  const size_t es = elem_size(d.dtype);
+  const size_t es = ac_elem_size(d.dtype);
   cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
   cuuint64_t strides[2] = {(cuuint64_t)(d.pitch_x * es), (cuuint64_t)(d.pitch_x * d.ny * es)};
   cuuint32_t box[3], estr[3] = {1, 1, 1};
@@ -147,7 +150,7 @@ static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) 
     box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
     rank = 3;
   }
-  CUresult r = fn(out, tmap_type(d.dtype), rank, base, dims, strides, box, estr,
+  CUresult r = fn(out, ac_tmap_type(d.dtype), rank, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(AC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -174,7 +177,7 @@ static void release_graph(ac_ctx *c) {
 
 extern "C" int ac_create(const ac_grid_desc *desc, void *phi_dev, void *workspace_dev,
                          void *cuda_stream, ac_ctx **out) {
-  int rc = validate_desc(desc);
+  int rc = ac_validate_desc(desc);
   if (rc) return rc;
   if (!out) return fail(AC_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -295,7 +298,7 @@ extern "C" int ac_get_schedule(ac_ctx *c, int32_t *variant, int32_t *k) {
 // remainder; an odd launch count is made even by splitting a launch of
 // depth >= 2, so that the result lands back in phi.  Returns false if the
 // count stays odd (all depths 1): the caller then copies ws -> phi.
-static bool plan_depths(int64_t n, int k, std::vector<int> &depths) {
+bool ac_plan_depths(int64_t n, int k, std::vector<int> &depths) {
   depths.clear();
   for (int64_t i = 0; i < n / k; ++i) depths.push_back(k);
   if (n % k) depths.push_back((int)(n % k));
@@ -313,7 +316,7 @@ static bool plan_depths(int64_t n, int k, std::vector<int> &depths) {
 
 static int issue_steps(ac_ctx *c, int64_t n, int variant, int k) {
   std::vector<int> depths;
-  const bool even = variant == AC_VARIANT_DIRECT ? (n % 2 == 0) : plan_depths(n, k, depths);
+  const bool even = variant == AC_VARIANT_DIRECT ? (n % 2 == 0) : ac_plan_depths(n, k, depths);
   if (variant == AC_VARIANT_DIRECT) depths.assign((size_t)n, 1);
   bool src_is_phi = true;
   for (int dep : depths) {
@@ -334,7 +337,7 @@ static int issue_steps(ac_ctx *c, int64_t n, int variant, int k) {
     src_is_phi = !src_is_phi;
   }
   if (!even) {
-    const size_t es = elem_size(c->d.dtype);
+    const size_t es = ac_elem_size(c->d.dtype);
     AC_CUDA(cudaMemcpy2DAsync(c->phi, c->d.pitch_x * es, c->ws, c->d.pitch_x * es, c->d.nx * es,
                               (size_t)(c->d.ny * c->d.nz), cudaMemcpyDeviceToDevice, c->stream));
   }
@@ -540,7 +543,7 @@ extern "C" int ac_set_graph(ac_ctx *c, int32_t enable) {
 // device buffer.
 extern "C" int ac_observe_noalloc(const ac_grid_desc *desc, const void *phi_dev, void *cuda_stream,
                                   double *out_dev) {
-  int rc = validate_desc(desc);
+  int rc = ac_validate_desc(desc);
   if (rc) return rc;
   if (!phi_dev || !out_dev) return fail(AC_ERR_INVALID, "phi_dev and out_dev must be non-NULL");
   if (((uintptr_t)phi_dev & 15) || ((uintptr_t)out_dev & 7))

@@ -55,4 +55,18 @@ cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double
 cudaError_t launch_init_random(int dtype, const GridParams &g, void *phi, uint64_t seed,
                                double amplitude, cudaStream_t s);
 
+// ---- helpers shared by the C-ABI translation units (defined in ac_api.cu)
+int set_error(int code, const char *msg);
+
 }  // namespace ac
+
+#include <vector>
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+int ac_validate_desc(const ac_grid_desc *d);
+bool ac_plan_depths(int64_t n, int k, std::vector<int> &depths);
+EncodeTiledFn ac_encode_fn();
+CUtensorMapDataType ac_tmap_type(int dtype);
+size_t ac_elem_size(int dtype);

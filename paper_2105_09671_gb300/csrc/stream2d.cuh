@@ -52,40 +52,42 @@ struct S2Geom {
   static constexpr int SMEM = kS2Warps * (RING_BYTES + kS2Stages * 8);
 };
 
+// One strip item: the columns [xs, xs + SW) of rows [y0, y1) advanced by K
+// steps, written for the columns [xs + hx, xs + SW - hx) of [y0, y1).
+struct S2Item {
+  int xs, y0, y1, hx;
+  int nx, ny;
+  int64_t pitch;
+};
+
+// Processes one item on the calling warp.  ring_smem / bars are the warp's
+// TMA ring (mbarriers already initialised); u counts the ring groups this
+// warp has consumed so far (stage u % D, phase (u / D) & 1) and is advanced
+// past this item.  Returns false if a bounded wait expired (the status word
+// is set and every copy this item issued has landed).
 template <typename T, int K, bool FASTX>
-__global__ void __launch_bounds__(kS2Warps * 32, 1)
-    stream2d_k(const __grid_constant__ CUtensorMap src_map, T *__restrict__ dst, GridParams g,
-               int n_strips, int n_chunks, int chunk_rows) {
+__device__ __forceinline__ bool s2_item(T *ring_smem, uint64_t *bars, uint32_t &u,
+                                        const CUtensorMap *src_map, T *__restrict__ dst,
+                                        const S2Item &it, typename Traits<T>::C alpha,
+                                        typename Traits<T>::C beta, int *status) {
   using Gm = S2Geom<T, K>;
   using C = typename Traits<T>::C;
-  constexpr int E = Gm::E, V = Gm::V, VPL = Gm::VPL;
+  constexpr int E = Gm::E, V = Gm::V, VPL = Gm::VPL, D = kS2Stages;
   constexpr uint32_t kStageBytes = Gm::STAGE_ELEMS * sizeof(T);
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T *ring_smem = reinterpret_cast<T *>(smem + warp * Gm::RING_BYTES);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kS2Warps * Gm::RING_BYTES) + warp * kS2Stages;
-
-  const int64_t gw = (int64_t)blockIdx.x * kS2Warps + warp;
-  if (gw >= (int64_t)n_strips * n_chunks) return;  // no CTA-wide barrier in this kernel
-  const int strip = (int)(gw % n_strips);
-  const int chunk = (int)(gw / n_strips);
-  const int xs = strip * Gm::OW - Gm::HX;  // first column of the strip (may be < 0)
-  const int ny = (int)g.ny, nx = (int)g.nx;
-  const int y0 = chunk * chunk_rows;
-  const int y1 = min(ny, y0 + chunk_rows);
+  const int lane = threadIdx.x & 31;
+  const int xs = it.xs, nx = it.nx, ny = it.ny, y0 = it.y0, y1 = it.y1;
   const int lo0 = max(0, y0 - K);
   const int hi0 = min(ny, y1 + K);
   const int n_in = hi0 - lo0;
   const int n_groups = (n_in + kS2Rows - 1) / kS2Rows;
   const int n_iter = y1 - lo0 + K;
+  const uint32_t u0 = u;
 
   if (lane == 0) {
-    tma_prefetch_desc(&src_map);
-    for (int s = 0; s < kS2Stages; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
-    for (int s = 0; s < kS2Stages && s < n_groups; ++s) {
+    for (int p = 0; p < D && p < n_groups; ++p) {
+      const int s = (int)((u0 + p) % D);
       mbar_arrive_expect_tx(&bars[s], kStageBytes);
-      tma_load_2d(ring_smem + s * Gm::STAGE_ELEMS, &src_map, &bars[s], xs, lo0 + s * kS2Rows);
+      tma_load_2d(ring_smem + s * Gm::STAGE_ELEMS, src_map, &bars[s], xs, lo0 + p * kS2Rows);
     }
   }
   __syncwarp();
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
     lfix[v] = xl + v * V == 0;
     rfix[v] = xl + v * V + V - 1 == nx - 1;
   }
-  const C alpha = (C)g.alpha, beta = (C)g.beta;
+  const int out_lo = xs + it.hx, out_hi = xs + Gm::SW - it.hx;
 
   // Level l keeps its last three rows in a ring of register slots: at
   // iteration t slot t%3 holds row R+1 (newest), (t+2)%3 row R and (t+1)%3
@@ -118,16 +120,16 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
     constexpr int SN = P, SB = (P + 2) % 3, SA = (P + 1) % 3;
     const int grp = t / kS2Rows;
     const int rr = t - grp * kS2Rows;
-    const int stg = grp % kS2Stages;
+    const int stg = (int)((u0 + grp) % D);
     if (!BND || t < n_in) {
       if (rr == 0) {
-        const bool ok = mbar_wait_bounded(&bars[stg], (uint32_t)(grp / kS2Stages) & 1u);
+        const bool ok = mbar_wait_bounded(&bars[stg], ((u0 + grp) / D) & 1u);
         if (!__all_sync(0xffffffffu, ok)) {
           // give up: record it, let every issued copy land, then leave
           if (lane == 0) {
-            report_timeout(g.status);
-            for (int q = grp + 1; q < n_groups && q < grp + kS2Stages; ++q)
-              mbar_wait_bounded(&bars[q % kS2Stages], (uint32_t)(q / kS2Stages) & 1u);
+            report_timeout(status);
+            for (int q = grp + 1; q < n_groups && q < grp + D; ++q)
+              mbar_wait_bounded(&bars[(u0 + q) % D], ((u0 + q) / D) & 1u);
           }
           __syncwarp();
           return false;
@@ -182,11 +184,11 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
       } else {
         const int RK = R;
         if (RK >= y0 && RK < y1) {
-          T *drow = dst + (int64_t)RK * g.pitch;
+          T *drow = dst + (int64_t)RK * it.pitch;
 #pragma unroll
           for (int v = 0; v < VPL; ++v) {
             const int xv = xl + v * V;
-            if (xv >= xs + Gm::HX && xv < xs + Gm::SW - Gm::HX && xv < nx) {
+            if (xv >= out_lo && xv < out_hi && xv < nx) {
               if (xv + V <= nx) {
                 *reinterpret_cast<uint4 *>(drow + xv) = pack16<T>(out + v * V);
               } else {
@@ -203,11 +205,11 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
     // the stage's last row has been consumed (its values used above): refill
     if (t < n_in && (rr == kS2Rows - 1 || t == n_in - 1)) {
       __syncwarp();
-      const int nxt = grp + kS2Stages;
+      const int nxt = grp + D;
       if (lane == 0 && nxt < n_groups) {
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bars[stg], kStageBytes);
-        tma_load_2d(ring_smem + stg * Gm::STAGE_ELEMS, &src_map, &bars[stg], xs, lo0 + nxt * kS2Rows);
+        tma_load_2d(ring_smem + stg * Gm::STAGE_ELEMS, src_map, &bars[stg], xs, lo0 + nxt * kS2Rows);
       }
     }
     return true;
@@ -219,20 +221,69 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
   const int bnd_lo_end = (lo0 == 0) ? K : -1;
   const int bnd_hi_begin = (hi0 == ny) ? ny - lo0 - 1 : n_iter;
   int t = 0;
-  for (; t + 3 <= n_iter; t += 3) {
+  bool ok = true;
+  for (; ok && t + 3 <= n_iter; t += 3) {
     const bool bnd = (t <= bnd_lo_end) || (t + 2 >= bnd_hi_begin);
     if (bnd) {
-      if (!body.template operator()<0, true>(t)) return;
-      if (!body.template operator()<1, true>(t + 1)) return;
-      if (!body.template operator()<2, true>(t + 2)) return;
+      ok = body.template operator()<0, true>(t) && body.template operator()<1, true>(t + 1) &&
+           body.template operator()<2, true>(t + 2);
     } else {
-      if (!body.template operator()<0, false>(t)) return;
-      if (!body.template operator()<1, false>(t + 1)) return;
-      if (!body.template operator()<2, false>(t + 2)) return;
+      ok = body.template operator()<0, false>(t) && body.template operator()<1, false>(t + 1) &&
+           body.template operator()<2, false>(t + 2);
     }
   }
-  if (t < n_iter && !body.template operator()<0, true>(t++)) return;
-  if (t < n_iter && !body.template operator()<1, true>(t++)) return;
+  if (ok && t < n_iter) ok = body.template operator()<0, true>(t++);
+  if (ok && t < n_iter) ok = body.template operator()<1, true>(t++);
+  u = u0 + (uint32_t)n_groups;
+  return ok;
+}
+
+// Per-warp TMA ring of the calling CTA: D stages and D mbarriers per warp.
+template <typename T>
+struct S2Ring {
+  T *smem;
+  uint64_t *bars;
+};
+template <typename T, int K>
+__device__ __forceinline__ S2Ring<T> s2_ring(unsigned char *smem, int warp) {
+  using Gm = S2Geom<T, K>;
+  S2Ring<T> r;
+  r.smem = reinterpret_cast<T *>(smem + warp * Gm::RING_BYTES);
+  r.bars = reinterpret_cast<uint64_t *>(smem + kS2Warps * Gm::RING_BYTES) + warp * kS2Stages;
+  return r;
+}
+
+template <typename T, int K, bool FASTX>
+__global__ void __launch_bounds__(kS2Warps * 32, 1)
+    stream2d_k(const __grid_constant__ CUtensorMap src_map, T *__restrict__ dst, GridParams g,
+               int n_strips, int n_chunks, int chunk_rows) {
+  using Gm = S2Geom<T, K>;
+  using C = typename Traits<T>::C;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const S2Ring<T> ring = s2_ring<T, K>(smem, warp);
+
+  const int64_t gw = (int64_t)blockIdx.x * kS2Warps + warp;
+  if (gw >= (int64_t)n_strips * n_chunks) return;  // no CTA-wide barrier in this kernel
+  const int strip = (int)(gw % n_strips);
+  const int chunk = (int)(gw / n_strips);
+  S2Item it;
+  it.xs = strip * Gm::OW - Gm::HX;  // first column of the strip (may be < 0)
+  it.hx = Gm::HX;
+  it.nx = (int)g.nx;
+  it.ny = (int)g.ny;
+  it.y0 = chunk * chunk_rows;
+  it.y1 = min(it.ny, it.y0 + chunk_rows);
+  it.pitch = g.pitch;
+
+  if (lane == 0) {
+    tma_prefetch_desc(&src_map);
+    for (int s = 0; s < kS2Stages; ++s) mbar_init(&ring.bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t u = 0;
+  s2_item<T, K, FASTX>(ring.smem, ring.bars, u, &src_map, dst, it, (C)g.alpha, (C)g.beta, g.status);
 }
 
 // ------------------------------------------------------------------ host ---

@@ -133,3 +133,92 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent 2D grids stepped by one persistent kernel launch.
+
+    ``specs`` is a list of (shape, h, eps, dt); every grid gets its own field
+    (a PyTorch tensor) and a slice of one shared workspace.  All grids share
+    one storage type and the stream.
+    """
+
+    def __init__(self, specs, dtype="f32", device="cuda", stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise L.AcError(L.AC_ERR_UNSUPPORTED, "a CUDA device is required")
+        self.code = _dtype_code(dtype)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        es = np.dtype(_NUMPY[self.code]).itemsize
+        per = 128 // es
+        self.shapes, self.descs, self.fields = [], [], []
+        tdt = _TORCH[self.code]
+        for shape, h, eps, dt in specs:
+            ny, nx = (int(shape[0]), int(shape[1]))
+            pitch = -(-nx // per) * per
+            self.shapes.append((ny, nx))
+            self.descs.append(L.make_desc(2, self.code, nx, ny, 1, pitch, float(h), float(eps), float(dt)))
+            self.fields.append(torch.zeros(ny * pitch, dtype=tdt, device=self.device))
+        nbytes = L.ac_batch_workspace_bytes(self.descs)
+        self._ws = torch.zeros(nbytes // es + 256 // es, dtype=tdt, device=self.device)
+        ws_ptr = self._ws.data_ptr()
+        ws_ptr = -(-ws_ptr // 256) * 256
+        self.handle = L.ac_batch_create(self.descs, [f.data_ptr() for f in self.fields], ws_ptr,
+                                        self.stream.cuda_stream)
+
+    def __len__(self):
+        return len(self.fields)
+
+    def phi(self, i: int) -> torch.Tensor:
+        ny, nx = self.shapes[i]
+        return self.fields[i].view(ny, -1)[:, :nx]
+
+    def load(self, i: int, array) -> None:
+        a = np.asarray(array)
+        t = torch.from_numpy(np.ascontiguousarray(a.astype(_NUMPY[self.code])))
+        with torch.cuda.stream(self.stream):
+            self.phi(i).copy_(t.to(self.device))
+
+    def to_numpy(self, i: int) -> np.ndarray:
+        self.stream.synchronize()
+        return self.phi(i).cpu().numpy().copy()
+
+    def step(self, n_per_instance) -> None:
+        if np.isscalar(n_per_instance):
+            n_per_instance = [int(n_per_instance)] * len(self)
+        L.ac_batch_step(self.handle, n_per_instance)
+
+    def set_schedule(self, k: int) -> None:
+        L.ac_batch_set_schedule(self.handle, k)
+
+    def schedule(self) -> int:
+        return L.ac_batch_get_schedule(self.handle)
+
+    def autotune(self, steps_per_trial: int = 64) -> None:
+        L.ac_batch_autotune(self.handle, steps_per_trial)
+
+    def set_graph(self, enable: bool) -> None:
+        L.ac_batch_set_graph(self.handle, enable)
+
+    def observe(self, i: int):
+        return L.ac_batch_observe(self.handle, i)
+
+    def status(self) -> int:
+        return L.ac_batch_status(self.handle)
+
+    def set_wait_limit(self, polls: int) -> None:
+        L.ac_batch_set_wait_limit(self.handle, polls)
+
+    def launch_count(self) -> int:
+        return L.ac_batch_launch_count(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            L.ac_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

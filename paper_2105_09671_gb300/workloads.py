@@ -77,3 +77,23 @@ def smooth_field(shape, seed: int, modes: int = 4, amp: float = 0.9) -> np.ndarr
         f += rng.uniform(-1, 1) * term
     m = np.max(np.abs(f))
     return amp * f / m if m > 0 else f
+
+
+def batch_instances(count: int = 512, seed: int = 0, steps: int = 2000):
+    """The batched workload: `count` independent 2D grids with sizes drawn
+    uniformly from {64, 96, ..., 1024}^2, h = 1/n, dt = 0.1 h^2, eps drawn
+    uniformly from [3h, 6h]; even indices hold a tanh circle of radius drawn
+    from [0.1, 0.4] centred at (0.5, 0.5), odd indices a random state of
+    amplitude 0.1 (SplitMix64 seed 1000 + index).  One seeded draw.
+    Returns dicts with n, h, eps, dt, init, r0, seed, steps."""
+    rng = np.random.default_rng(seed)
+    sizes = np.arange(64, 1025, 32)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        h = 1.0 / n
+        eps = float(rng.uniform(3.0, 6.0)) * h
+        r0 = float(rng.uniform(0.1, 0.4))
+        out.append(dict(n=n, h=h, eps=eps, dt=0.1 * h * h, init="sphere" if i % 2 == 0 else "random",
+                        r0=r0, seed=1000 + i, steps=steps))
+    return out

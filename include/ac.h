@@ -178,6 +178,17 @@ int ac_status(ac_ctx *ctx);
  * number of single-step passes is a copy, not a kernel, and is not counted. */
 int ac_launch_count(ac_ctx *ctx, int64_t *out);
 
+/* ------------------------------------------------ tensor-core building block */
+/* D[m x 32] = A[m x k] * B[32 x k]^T with BF16 operands (row-major, k
+ * contiguous) and FP32 accumulation on the 5th-generation tensor cores
+ * (tcgen05, accumulator in tensor memory).  m a multiple of 128, k a multiple
+ * of 16 in [16, 512]; all pointers device memory, 16-byte aligned.  The
+ * learned stepper's convolutions are built from the same primitive (their
+ * reduction dimension is 9 or 27 taps x 32 channels); exposed so the operand
+ * layout can be verified on its own.  Asynchronous on cuda_stream. */
+int ac_tc_gemm_bf16_n32(const void *a_dev, const void *b_dev, float *d_dev, int64_t m,
+                        int32_t k, void *cuda_stream);
+
 /* ------------------------------------------------------ batched mode ---- */
 /* Many independent 2D grids (each its own size, eps, dt and state) advanced
  * together by ONE persistent kernel launch (the paper runs one

@@ -32,6 +32,7 @@ EXPORTED = (
     "ac_batch_workspace_bytes", "ac_batch_create", "ac_batch_step", "ac_batch_set_schedule",
     "ac_batch_get_schedule", "ac_batch_autotune", "ac_batch_set_graph", "ac_batch_observe",
     "ac_batch_status", "ac_batch_set_wait_limit", "ac_batch_launch_count", "ac_batch_destroy",
+    "ac_tc_gemm_bf16_n32",
 )
 
 
@@ -101,6 +102,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_batch_set_wait_limit": [vp, ctypes.c_uint32],
         "ac_batch_launch_count": [vp, ctypes.POINTER(i64)],
         "ac_batch_destroy": [vp],
+        "ac_tc_gemm_bf16_n32": [vp, vp, vp, i64, i32, vp],
         "ac_destroy": [vp],
     }
     for name, args in sig.items():
@@ -290,3 +292,8 @@ def ac_batch_launch_count(batch: int) -> int:
 
 def ac_batch_destroy(batch: int) -> None:
     check(lib().ac_batch_destroy(ctypes.c_void_p(batch)))
+
+
+def ac_tc_gemm_bf16_n32(a_ptr: int, b_ptr: int, d_ptr: int, m: int, k: int, stream_ptr: int) -> None:
+    check(lib().ac_tc_gemm_bf16_n32(ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
+                                    ctypes.c_void_p(d_ptr), int(m), int(k), ctypes.c_void_p(stream_ptr)))

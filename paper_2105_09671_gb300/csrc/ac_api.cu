@@ -570,6 +570,21 @@ extern "C" int ac_observe_noalloc(const ac_grid_desc *desc, const void *phi_dev,
   return AC_OK;
 }
 
+extern "C" int ac_tc_gemm_bf16_n32(const void *a_dev, const void *b_dev, float *d_dev, int64_t m,
+                                   int32_t k, void *cuda_stream) {
+  if (!a_dev || !b_dev || !d_dev) return fail(AC_ERR_INVALID, "NULL operand");
+  if (m < 128 || m % 128 || k < 16 || k > 512 || k % 16)
+    return fail(AC_ERR_INVALID, "need m a multiple of 128 and k a multiple of 16 in [16, 512]");
+  if (((uintptr_t)a_dev | (uintptr_t)b_dev | (uintptr_t)d_dev) & 15)
+    return fail(AC_ERR_INVALID, "operands must be 16-byte aligned");
+  static int *status = nullptr;
+  if (!status && cudaMalloc(&status, sizeof(int)) != cudaSuccess)
+    return fail(AC_ERR_NOMEM, "status word allocation failed");
+  cudaError_t e = launch_tc_gemm_n32(a_dev, b_dev, d_dev, m, k, status, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "tensor-core GEMM launch failed: %s", cudaGetErrorString(e));
+  return AC_OK;
+}
+
 extern "C" int ac_launch_count(ac_ctx *c, int64_t *out) {
   if (!c || !out) return fail(AC_ERR_INVALID, "NULL argument");
   *out = c->launches;

@@ -55,6 +55,11 @@ cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double
 cudaError_t launch_init_random(int dtype, const GridParams &g, void *phi, uint64_t seed,
                                double amplitude, cudaStream_t s);
 
+// D[m x 32] = A[m x k] * B[32 x k]^T on the tensor cores (BF16 in, FP32 out);
+// m a multiple of 128, k a multiple of 16 in [16, 512].
+cudaError_t launch_tc_gemm_n32(const void *a, const void *b, float *d, int64_t m, int k, int *status,
+                               cudaStream_t s);
+
 // ---- helpers shared by the C-ABI translation units (defined in ac_api.cu)
 int set_error(int code, const char *msg);
 

@@ -189,6 +189,69 @@ int ac_launch_count(ac_ctx *ctx, int64_t *out);
 int ac_tc_gemm_bf16_n32(const void *a_dev, const void *b_dev, float *d_dev, int64_t m,
                         int32_t k, void *cuda_stream);
 
+/* --------------------------------------------------- learned stepper ---- */
+/* A small convolutional network that jumps n (default 16) explicit Euler
+ * steps at once, trained on trajectories of the plain stepper, with the
+ * plain stepper as its fallback (not in the paper; its building block is the
+ * paper's replicate padding + convolution of Section 2.2).  Definition:
+ *   z1 = conv(phi, W1) + b1, a1 = gelu(z1)            1 -> 32 channels
+ *   zl = conv(a_{l-1}, Wl) + bl, al = gelu(zl)         32 -> 32, l = 2..5
+ *   z6 = conv(a5, W6) + b6                             32 -> 1
+ *   phi_hat = phi + s * z6,   s = n dt / eps^2
+ * conv = 3x3 (2D) or 3x3x3 (3D) cross-correlation with replicate padding;
+ * gelu(x) = x/2 (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))).  Activations are
+ * BF16, accumulation FP32; the 32 -> 32 layers (forward, data and weight
+ * gradients) run as implicit GEMMs on the tcgen05 tensor cores.
+ * Parameters: one flat FP32 vector, per layer W[t][ci][co] then b[co],
+ * taps t over offsets (-1, 0, 1)^d with x fastest.
+ * Fields: FP32, contiguous [batch][nz][ny][nx] device arrays. */
+typedef struct ac_net ac_net; /* opaque */
+
+typedef struct {
+  int32_t steps_per_jump; /* n: Euler steps one learned jump stands for            */
+  double energy_rtol;     /* accept if E(phi_hat) <= E(phi) (1 + energy_rtol)       */
+  double max_abs;         /* accept if max |phi_hat| <= max_abs                     */
+  double residual_tol;    /* accept if max |phi_hat - phi - n dt RHS(phi)| <= this
+                             (<= 0 disables the check)                              */
+} ac_guard;
+
+int ac_net_param_count(int32_t ndim, int64_t *out);
+/* ndim 2 or 3; parameters start at zero (set them with ac_net_set_params).
+ * Allocates parameter, gradient and optimiser buffers; per-shape activation
+ * buffers are allocated on first use of a shape and kept until destroy. */
+int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out);
+/* Copy count (= ac_net_param_count) FP32 parameters from / to host memory;
+ * setting them also resets the Adam moments.  Synchronise. */
+int ac_net_set_params(ac_net *net, const float *host_params, int64_t count);
+int ac_net_get_params(ac_net *net, float *host_params, int64_t count);
+/* out = phi + scale * NN(phi) for batch fields of nx x ny x nz (nz = 1 in
+ * 2D).  phi and out must not overlap.  Asynchronous. */
+int ac_net_forward(ac_net *net, const float *phi_dev, float *out_dev, int32_t batch, int64_t nx,
+                   int64_t ny, int64_t nz, double scale);
+/* Mean over cells of ((phi + scale NN(phi) - target) / scale)^2 and its
+ * gradient wrt every parameter (kept for ac_net_adam; copied to grads_host
+ * when non-NULL).  Synchronises; *loss is the mean. */
+int ac_net_loss_grads(ac_net *net, const float *phi_dev, const float *target_dev, int32_t batch,
+                      int64_t nx, int64_t ny, int64_t nz, double scale, double *loss,
+                      float *grads_host);
+/* One Adam step (Kingma & Ba 2015, bias-corrected) with the last gradients. */
+int ac_net_adam(ac_net *net, double lr, double beta1, double beta2, double eps);
+/* ac_net_loss_grads + ac_net_adam(lr, 0.9, 0.999, 1e-8). */
+int ac_net_train_step(ac_net *net, const float *phi_dev, const float *target_dev, int32_t batch,
+                      int64_t nx, int64_t ny, int64_t nz, double scale, double lr, double *loss);
+int ac_net_launch_count(ac_net *net, int64_t *out);
+int ac_net_destroy(ac_net *net);
+
+/* Advance the context's field (FP32, pitch_x == nx, same stream as the net)
+ * by `jumps` learned jumps of guard->steps_per_jump steps each.  Every jump
+ * is checked: finite values, energy not above E(phi)(1 + energy_rtol), max
+ * |phi_hat| <= max_abs and the residual check; a rejected jump is replaced by
+ * that many plain steps (ac_step).  *fallbacks (if non-NULL) receives the
+ * number of rejected jumps.  Uses the context's workspace; synchronises once
+ * per jump. */
+int ac_learned_advance(ac_ctx *ctx, ac_net *net, int64_t jumps, const ac_guard *guard,
+                       int64_t *fallbacks);
+
 /* ------------------------------------------------------ batched mode ---- */
 /* Many independent 2D grids (each its own size, eps, dt and state) advanced
  * together by ONE persistent kernel launch (the paper runs one

@@ -33,6 +33,9 @@ EXPORTED = (
     "ac_batch_get_schedule", "ac_batch_autotune", "ac_batch_set_graph", "ac_batch_observe",
     "ac_batch_status", "ac_batch_set_wait_limit", "ac_batch_launch_count", "ac_batch_destroy",
     "ac_tc_gemm_bf16_n32",
+    "ac_net_param_count", "ac_net_create", "ac_net_set_params", "ac_net_get_params",
+    "ac_net_forward", "ac_net_loss_grads", "ac_net_adam", "ac_net_train_step",
+    "ac_net_launch_count", "ac_net_destroy", "ac_learned_advance",
 )
 
 
@@ -50,6 +53,15 @@ class AcGridDesc(ctypes.Structure):
     ]
 
 
+class AcGuard(ctypes.Structure):
+    _fields_ = [
+        ("steps_per_jump", ctypes.c_int32),
+        ("energy_rtol", ctypes.c_double),
+        ("max_abs", ctypes.c_double),
+        ("residual_tol", ctypes.c_double),
+    ]
+
+
 class AcError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[ac error {code}] {msg}")
@@ -57,6 +69,7 @@ class AcError(RuntimeError):
 
 
 _lib = None
+_build_error = None
 
 
 def lib_path() -> str:
@@ -65,10 +78,16 @@ def lib_path() -> str:
 
 def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     """Load libac.so (building it first if missing or stale)."""
-    global _lib
+    global _lib, _build_error
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_missing else _build.LIB
+    if _build_error is not None:  # do not rebuild on every call after a failure
+        raise _build_error
+    try:
+        path = _build.build() if build_if_missing else _build.LIB
+    except Exception as e:  # noqa: BLE001 - surfaced to the caller unchanged
+        _build_error = e
+        raise
     if not os.path.exists(path):
         raise AcError(AC_ERR_UNSUPPORTED, f"CUDA library not built: {path}")
     L = ctypes.CDLL(path)
@@ -103,6 +122,17 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_batch_launch_count": [vp, ctypes.POINTER(i64)],
         "ac_batch_destroy": [vp],
         "ac_tc_gemm_bf16_n32": [vp, vp, vp, i64, i32, vp],
+        "ac_net_param_count": [i32, ctypes.POINTER(i64)],
+        "ac_net_create": [i32, vp, ctypes.POINTER(vp)],
+        "ac_net_set_params": [vp, vp, i64],
+        "ac_net_get_params": [vp, vp, i64],
+        "ac_net_forward": [vp, vp, vp, i32, i64, i64, i64, dbl],
+        "ac_net_loss_grads": [vp, vp, vp, i32, i64, i64, i64, dbl, ctypes.POINTER(dbl), vp],
+        "ac_net_adam": [vp, dbl, dbl, dbl, dbl],
+        "ac_net_train_step": [vp, vp, vp, i32, i64, i64, i64, dbl, dbl, ctypes.POINTER(dbl)],
+        "ac_net_launch_count": [vp, ctypes.POINTER(i64)],
+        "ac_net_destroy": [vp],
+        "ac_learned_advance": [vp, vp, i64, ctypes.POINTER(AcGuard), ctypes.POINTER(i64)],
         "ac_destroy": [vp],
     }
     for name, args in sig.items():
@@ -297,3 +327,83 @@ def ac_batch_destroy(batch: int) -> None:
 def ac_tc_gemm_bf16_n32(a_ptr: int, b_ptr: int, d_ptr: int, m: int, k: int, stream_ptr: int) -> None:
     check(lib().ac_tc_gemm_bf16_n32(ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
                                     ctypes.c_void_p(d_ptr), int(m), int(k), ctypes.c_void_p(stream_ptr)))
+
+
+# ---------------------------------------------------------- learned stepper --
+
+def ac_net_param_count(ndim: int) -> int:
+    out = ctypes.c_int64()
+    check(lib().ac_net_param_count(int(ndim), ctypes.byref(out)))
+    return out.value
+
+
+def ac_net_create(ndim: int, stream_ptr: int) -> int:
+    h = ctypes.c_void_p()
+    check(lib().ac_net_create(int(ndim), ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def ac_net_set_params(net: int, params_f32) -> None:
+    import numpy as np
+    a = np.ascontiguousarray(params_f32, dtype=np.float32)
+    check(lib().ac_net_set_params(ctypes.c_void_p(net), a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+
+def ac_net_get_params(net: int, count: int):
+    import numpy as np
+    a = np.empty(count, dtype=np.float32)
+    check(lib().ac_net_get_params(ctypes.c_void_p(net), a.ctypes.data_as(ctypes.c_void_p), count))
+    return a
+
+
+def ac_net_forward(net: int, phi_ptr: int, out_ptr: int, batch: int, nx: int, ny: int, nz: int,
+                   scale: float) -> None:
+    check(lib().ac_net_forward(ctypes.c_void_p(net), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(out_ptr),
+                               int(batch), int(nx), int(ny), int(nz), float(scale)))
+
+
+def ac_net_loss_grads(net: int, phi_ptr: int, target_ptr: int, batch: int, nx: int, ny: int, nz: int,
+                      scale: float, want_grads: bool = False):
+    import numpy as np
+    loss = ctypes.c_double()
+    grads = None
+    gp = None
+    if want_grads:
+        cnt = ctypes.c_int64()
+        # parameter count of this network's dimension: nz > 1 means 3D
+        check(lib().ac_net_param_count(3 if nz > 1 else 2, ctypes.byref(cnt)))
+        grads = np.empty(cnt.value, dtype=np.float32)
+        gp = grads.ctypes.data_as(ctypes.c_void_p)
+    check(lib().ac_net_loss_grads(ctypes.c_void_p(net), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(target_ptr),
+                                  int(batch), int(nx), int(ny), int(nz), float(scale), ctypes.byref(loss), gp))
+    return loss.value, grads
+
+
+def ac_net_adam(net: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    check(lib().ac_net_adam(ctypes.c_void_p(net), float(lr), float(beta1), float(beta2), float(eps)))
+
+
+def ac_net_train_step(net: int, phi_ptr: int, target_ptr: int, batch: int, nx: int, ny: int, nz: int,
+                      scale: float, lr: float) -> float:
+    loss = ctypes.c_double()
+    check(lib().ac_net_train_step(ctypes.c_void_p(net), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(target_ptr),
+                                  int(batch), int(nx), int(ny), int(nz), float(scale), float(lr),
+                                  ctypes.byref(loss)))
+    return loss.value
+
+
+def ac_net_launch_count(net: int) -> int:
+    out = ctypes.c_int64()
+    check(lib().ac_net_launch_count(ctypes.c_void_p(net), ctypes.byref(out)))
+    return out.value
+
+
+def ac_net_destroy(net: int) -> None:
+    check(lib().ac_net_destroy(ctypes.c_void_p(net)))
+
+
+def ac_learned_advance(ctx: int, net: int, jumps: int, guard: "AcGuard") -> int:
+    fb = ctypes.c_int64()
+    check(lib().ac_learned_advance(ctypes.c_void_p(ctx), ctypes.c_void_p(net), int(jumps),
+                                   ctypes.byref(guard), ctypes.byref(fb)))
+    return fb.value

@@ -1,0 +1,336 @@
+// C ABI of the learned 16-step jump network: parameters, forward pass,
+// loss and gradients, Adam, and the guarded learned advance of a context.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+#include "net.cuh"
+
+using namespace ac;
+
+static int nfail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return set_error(code, buf);
+}
+
+#define NC_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return nfail(AC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+struct ShapeBufs {
+  bool valid = false;
+  bool train = false;
+  NetShape sh{};
+  NetBuffers nb;  // activation / gradient pointers for this shape
+  float *phihat = nullptr;
+};
+
+struct ac_net {
+  int ndim = 2;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  NetBuffers base;  // params, grads, moments, packed weights, status, loss
+  ShapeBufs infer, train;
+  int adam_step = 0;
+  bool grads_valid = false;
+  unsigned int *guard = nullptr;  // 2 words: guard maxima
+  int64_t launches = 0;
+};
+
+static void free_shape(ShapeBufs &s) {
+  for (int i = 0; i < 5; ++i) {
+    cudaFree(s.nb.a[i]);
+    cudaFree(s.nb.z[i]);
+    cudaFree(s.nb.gz[i]);
+    s.nb.a[i] = s.nb.z[i] = s.nb.gz[i] = nullptr;
+  }
+  cudaFree(s.nb.raw);
+  cudaFree(s.nb.g6);
+  cudaFree(s.phihat);
+  s.nb.raw = s.nb.g6 = s.phihat = nullptr;
+  s.valid = false;
+}
+
+static bool same_shape(const NetShape &a, const NetShape &b) {
+  return a.ndim == b.ndim && a.batch == b.batch && a.nx == b.nx && a.ny == b.ny && a.nz == b.nz;
+}
+
+// Per-shape buffers: inference keeps two padded activations; training keeps
+// all five, the pre-activations, the padded gradients (zero ghost ring, set
+// once here) and the FP32 scratch.
+static int ensure_shape(ac_net *net, ShapeBufs &s, const NetShape &sh, bool train) {
+  if (s.valid && same_shape(s.sh, sh) && s.train == train) return AC_OK;
+  free_shape(s);
+  const size_t act = (size_t)sh.padded_cells() * kNetC * sizeof(bf16);
+  const size_t zb = (size_t)sh.cells() * kNetC * sizeof(bf16);
+  const int na = train ? 5 : 2;
+  for (int i = 0; i < na; ++i) NC_CUDA(cudaMalloc(&s.nb.a[i], act));
+  if (train) {
+    for (int i = 0; i < 5; ++i) {
+      NC_CUDA(cudaMalloc(&s.nb.z[i], zb));
+      NC_CUDA(cudaMalloc(&s.nb.gz[i], act));
+      NC_CUDA(cudaMemset(s.nb.gz[i], 0, act));
+    }
+    NC_CUDA(cudaMalloc(&s.nb.raw, (size_t)sh.cells() * kNetC * sizeof(float)));
+    NC_CUDA(cudaMalloc(&s.nb.g6, (size_t)sh.cells() * sizeof(float)));
+    NC_CUDA(cudaMalloc(&s.phihat, (size_t)sh.cells() * sizeof(float)));
+  }
+  s.sh = sh;
+  s.train = train;
+  s.valid = true;
+  return AC_OK;
+}
+
+static NetBuffers merged(const ac_net *net, const ShapeBufs &s) {
+  NetBuffers nb = net->base;
+  for (int i = 0; i < 5; ++i) {
+    nb.a[i] = s.nb.a[i];
+    nb.z[i] = s.nb.z[i];
+    nb.gz[i] = s.nb.gz[i];
+  }
+  nb.raw = s.nb.raw;
+  nb.g6 = s.nb.g6;
+  return nb;
+}
+
+static int check_shape(int ndim, int32_t batch, int64_t nx, int64_t ny, int64_t nz, NetShape *sh) {
+  if (batch < 1 || nx < 1 || ny < 1 || nz < 1) return nfail(AC_ERR_INVALID, "batch and sizes must be >= 1");
+  if (ndim == 2 && nz != 1) return nfail(AC_ERR_INVALID, "2D networks need nz == 1");
+  if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+    return nfail(AC_ERR_INVALID, "grid extent too large");
+  sh->ndim = ndim;
+  sh->batch = batch;
+  sh->nx = (int)nx;
+  sh->ny = (int)ny;
+  sh->nz = (int)nz;
+  return AC_OK;
+}
+
+extern "C" int ac_net_param_count(int32_t ndim, int64_t *out) {
+  if ((ndim != 2 && ndim != 3) || !out) return nfail(AC_ERR_INVALID, "ndim must be 2 or 3");
+  *out = net_layout(ndim).total;
+  return AC_OK;
+}
+
+extern "C" int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out) {
+  if (!out) return nfail(AC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return nfail(AC_ERR_INVALID, "ndim must be 2 or 3");
+  ac_net *net = new (std::nothrow) ac_net();
+  if (!net) return nfail(AC_ERR_NOMEM, "out of host memory");
+  net->ndim = ndim;
+  net->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&net->device);
+  cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, net->device);
+  NetBuffers &b = net->base;
+  b.layout = net_layout(ndim);
+  const size_t pbytes = (size_t)b.layout.total * sizeof(float);
+  const size_t wbytes = (size_t)4 * kNetC * b.layout.T * kNetC * sizeof(bf16);
+  cudaError_t e = cudaMalloc(&b.params, pbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.grads, pbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.m, pbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.v, pbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.wf, wbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.wd, wbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b.loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&net->guard, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b.params, 0, pbytes);
+  if (e == cudaSuccess) e = cudaMemset(b.m, 0, pbytes);
+  if (e == cudaSuccess) e = cudaMemset(b.v, 0, pbytes);
+  if (e == cudaSuccess) e = cudaMemset(b.status, 0, sizeof(int));
+  if (e == cudaSuccess) e = net_pack(b, net->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  if (e != cudaSuccess) {
+    cudaFree(b.params); cudaFree(b.grads); cudaFree(b.m); cudaFree(b.v);
+    cudaFree(b.wf); cudaFree(b.wd); cudaFree(b.loss); cudaFree(b.status); cudaFree(net->guard);
+    delete net;
+    cudaGetLastError();
+    return nfail(AC_ERR_NOMEM, "network allocation failed: %s", cudaGetErrorString(e));
+  }
+  *out = net;
+  return AC_OK;
+}
+
+extern "C" int ac_net_destroy(ac_net *net) {
+  if (!net) return AC_OK;
+  cudaStreamSynchronize(net->stream);
+  free_shape(net->infer);
+  free_shape(net->train);
+  NetBuffers &b = net->base;
+  cudaFree(b.params); cudaFree(b.grads); cudaFree(b.m); cudaFree(b.v);
+  cudaFree(b.wf); cudaFree(b.wd); cudaFree(b.loss); cudaFree(b.status); cudaFree(net->guard);
+  delete net;
+  return AC_OK;
+}
+
+extern "C" int ac_net_set_params(ac_net *net, const float *host_params, int64_t count) {
+  if (!net || !host_params) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (count != net->base.layout.total)
+    return nfail(AC_ERR_INVALID, "expected %lld parameters, got %lld",
+                 (long long)net->base.layout.total, (long long)count);
+  NC_CUDA(cudaStreamSynchronize(net->stream));
+  NC_CUDA(cudaMemcpy(net->base.params, host_params, count * sizeof(float), cudaMemcpyHostToDevice));
+  const size_t pbytes = (size_t)count * sizeof(float);
+  NC_CUDA(cudaMemset(net->base.m, 0, pbytes));
+  NC_CUDA(cudaMemset(net->base.v, 0, pbytes));
+  net->adam_step = 0;
+  net->grads_valid = false;
+  NC_CUDA(net_pack(net->base, net->stream));
+  ++net->launches;
+  NC_CUDA(cudaStreamSynchronize(net->stream));
+  return AC_OK;
+}
+
+extern "C" int ac_net_get_params(ac_net *net, float *host_params, int64_t count) {
+  if (!net || !host_params) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (count != net->base.layout.total) return nfail(AC_ERR_INVALID, "wrong parameter count");
+  NC_CUDA(cudaStreamSynchronize(net->stream));
+  NC_CUDA(cudaMemcpy(host_params, net->base.params, count * sizeof(float), cudaMemcpyDeviceToHost));
+  return AC_OK;
+}
+
+extern "C" int ac_net_forward(ac_net *net, const float *phi_dev, float *out_dev, int32_t batch,
+                              int64_t nx, int64_t ny, int64_t nz, double scale) {
+  if (!net || !phi_dev || !out_dev) return nfail(AC_ERR_INVALID, "NULL argument");
+  NetShape sh;
+  int rc = check_shape(net->ndim, batch, nx, ny, nz, &sh);
+  if (rc) return rc;
+  rc = ensure_shape(net, net->infer, sh, false);
+  if (rc) return rc;
+  cudaError_t e = net_forward(merged(net, net->infer), sh, phi_dev, (float)scale, out_dev, nullptr,
+                              false, net->num_sms, net->stream);
+  if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "network forward failed: %s", cudaGetErrorString(e));
+  net->launches += 6;
+  return AC_OK;
+}
+
+extern "C" int ac_net_loss_grads(ac_net *net, const float *phi_dev, const float *target_dev,
+                                 int32_t batch, int64_t nx, int64_t ny, int64_t nz, double scale,
+                                 double *loss, float *grads_host) {
+  if (!net || !phi_dev || !target_dev || !loss) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (!(scale > 0)) return nfail(AC_ERR_INVALID, "scale must be > 0");
+  NetShape sh;
+  int rc = check_shape(net->ndim, batch, nx, ny, nz, &sh);
+  if (rc) return rc;
+  rc = ensure_shape(net, net->train, sh, true);
+  if (rc) return rc;
+  const NetBuffers nb = merged(net, net->train);
+  NC_CUDA(cudaMemsetAsync(nb.loss, 0, sizeof(double), net->stream));
+  NC_CUDA(cudaMemsetAsync(nb.grads, 0, (size_t)nb.layout.total * sizeof(float), net->stream));
+  cudaError_t e = net_forward(nb, sh, phi_dev, (float)scale, net->train.phihat, target_dev, true,
+                              net->num_sms, net->stream);
+  if (e == cudaSuccess) e = net_backward(nb, sh, phi_dev, net->num_sms, net->stream);
+  if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "network training pass failed: %s", cudaGetErrorString(e));
+  net->launches += 6 + 1 + 4 * 3 + 1;
+  double h = 0.0;
+  NC_CUDA(cudaMemcpyAsync(&h, nb.loss, sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+  NC_CUDA(cudaStreamSynchronize(net->stream));
+  *loss = h / (double)sh.cells();
+  int st = 0;
+  NC_CUDA(cudaMemcpy(&st, nb.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    NC_CUDA(cudaMemset(nb.status, 0, sizeof(int)));
+    return nfail(AC_ERR_TIMEOUT, "a bounded tensor-core wait expired");
+  }
+  if (grads_host)
+    NC_CUDA(cudaMemcpy(grads_host, nb.grads, (size_t)nb.layout.total * sizeof(float), cudaMemcpyDeviceToHost));
+  net->grads_valid = true;
+  return AC_OK;
+}
+
+extern "C" int ac_net_adam(ac_net *net, double lr, double beta1, double beta2, double eps) {
+  if (!net) return nfail(AC_ERR_INVALID, "net is NULL");
+  if (!net->grads_valid) return nfail(AC_ERR_INVALID, "no gradients: call ac_net_loss_grads first");
+  if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return nfail(AC_ERR_INVALID, "invalid Adam hyper-parameters");
+  ++net->adam_step;
+  cudaError_t e = net_adam(net->base, (float)lr, (float)beta1, (float)beta2, (float)eps,
+                           net->adam_step, net->stream);
+  if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "Adam update failed: %s", cudaGetErrorString(e));
+  net->launches += 2;
+  return AC_OK;
+}
+
+extern "C" int ac_net_train_step(ac_net *net, const float *phi_dev, const float *target_dev,
+                                 int32_t batch, int64_t nx, int64_t ny, int64_t nz, double scale,
+                                 double lr, double *loss) {
+  int rc = ac_net_loss_grads(net, phi_dev, target_dev, batch, nx, ny, nz, scale, loss, nullptr);
+  if (rc) return rc;
+  return ac_net_adam(net, lr, 0.9, 0.999, 1e-8);
+}
+
+extern "C" int ac_net_launch_count(ac_net *net, int64_t *out) {
+  if (!net || !out) return nfail(AC_ERR_INVALID, "NULL argument");
+  *out = net->launches;
+  return AC_OK;
+}
+
+// ------------------------------------------------------ guarded advance ----
+extern "C" int ac_learned_advance(ac_ctx *c, ac_net *net, int64_t jumps, const ac_guard *guard,
+                                  int64_t *fallbacks) {
+  if (!c || !net || !guard) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (jumps < 0) return nfail(AC_ERR_INVALID, "jumps must be >= 0");
+  if (c->d.dtype != AC_F32) return nfail(AC_ERR_UNSUPPORTED, "the learned stepper runs on FP32 fields");
+  if (c->d.ndim != net->ndim) return nfail(AC_ERR_INVALID, "network and grid dimensions differ");
+  if (c->d.pitch_x != c->d.nx) return nfail(AC_ERR_UNSUPPORTED, "the learned stepper needs pitch_x == nx");
+  if (guard->steps_per_jump < 1) return nfail(AC_ERR_INVALID, "steps_per_jump must be >= 1");
+  if (c->stream != net->stream) return nfail(AC_ERR_INVALID, "context and network must share a stream");
+  const int n = guard->steps_per_jump;
+  const double scale = n * c->gp.alpha;  // s = n dt / eps^2
+  float *phi = static_cast<float *>(c->phi);
+  float *phat = static_cast<float *>(c->ws);
+  unsigned int *gbuf = net->guard;
+  int64_t fb = 0;
+  double e_cur = 0.0, obs[3];
+  int rc = ac_observe(c, obs);
+  if (rc) return rc;
+  e_cur = obs[0];
+  for (int64_t j = 0; j < jumps; ++j) {
+    rc = ac_net_forward(net, phi, phat, 1, c->d.nx, c->d.ny, c->d.nz, scale);
+    if (rc) return rc;
+    cudaError_t e = launch_guard(phi, phat, c->gp, c->d.ndim, n, gbuf, c->stream);
+    if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "guard launch failed: %s", cudaGetErrorString(e));
+    unsigned int gh[2];
+    NC_CUDA(cudaMemcpyAsync(gh, gbuf, sizeof gh, cudaMemcpyDeviceToHost, c->stream));
+    // energy of phi_hat (FP64 reduction over the workspace)
+    e = launch_observe(c->d.dtype, c->gp, phat, c->d_partials, c->d_out, c->stream);
+    if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(e));
+    NC_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NC_CUDA(cudaStreamSynchronize(c->stream));
+    c->launches += 3;
+    float mabs, mres;
+    memcpy(&mabs, &gh[0], 4);
+    memcpy(&mres, &gh[1], 4);
+    const double hd = c->d.ndim == 3 ? c->d.h * c->d.h * c->d.h : c->d.h * c->d.h;
+    const double e_new = hd * (c->h_out[0] / (c->d.eps * c->d.eps) + 0.5 * c->h_out[1] / (c->d.h * c->d.h));
+    const bool finite = c->h_out[3] == 0.0 && std::isfinite(e_new);
+    const bool ok = finite && e_new <= e_cur * (1.0 + guard->energy_rtol) + 1e-300 &&
+                    mabs <= guard->max_abs &&
+                    (guard->residual_tol <= 0 || mres <= guard->residual_tol);
+    if (ok) {
+      const size_t bytes = (size_t)c->d.nx * c->d.ny * c->d.nz * sizeof(float);
+      NC_CUDA(cudaMemcpyAsync(phi, phat, bytes, cudaMemcpyDeviceToDevice, c->stream));
+      e_cur = e_new;
+    } else {
+      ++fb;
+      rc = ac_step(c, n);  // the plain stepper takes over for this jump
+      if (rc) return rc;
+      rc = ac_observe(c, obs);
+      if (rc) return rc;
+      e_cur = obs[0];
+    }
+  }
+  if (fallbacks) *fallbacks = fb;
+  return AC_OK;
+}

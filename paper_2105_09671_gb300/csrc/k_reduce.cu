@@ -182,3 +182,54 @@ cudaError_t launch_observe_noalloc(int dtype, const GridParams &g, const void *p
 }
 
 }  // namespace ac
+
+namespace ac {
+
+// Guard quantities of a learned jump phi -> phi_hat over n Euler steps:
+//   out[0] = max |phi_hat|,
+//   out[1] = max |phi_hat - phi - n dt RHS(phi)|,
+// with dt RHS(phi) = beta (nsum - 2d phi) + alpha (phi - phi^3) the increment
+// of one explicit Euler step of Eq. (pytorchACeq) (clamped neighbours).
+// FP32 inputs with pitch == nx; maxima are formed on the absolute values'
+// bit patterns (non-negative floats order as unsigned integers).
+__global__ void __launch_bounds__(256) guard_kernel(const float *__restrict__ phi,
+                                                    const float *__restrict__ phat, GridParams g,
+                                                    int ndim, float nsteps,
+                                                    unsigned int *__restrict__ out) {
+  float mabs = 0.f, mres = 0.f;
+  const int64_t n = g.nx * g.ny * g.nz;
+  const float a = (float)g.alpha, b = (float)g.beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i % g.nx, r = i / g.nx, y = r % g.ny, z = r / g.ny;
+    const float p = phi[i];
+    float s = phi[i - x + (x > 0 ? x - 1 : 0)] + phi[i - x + (x + 1 < g.nx ? x + 1 : x)];
+    s += phi[i + ((y > 0 ? y - 1 : 0) - y) * g.nx] + phi[i + ((y + 1 < g.ny ? y + 1 : y) - y) * g.nx];
+    if (ndim == 3)
+      s += phi[i + ((z > 0 ? z - 1 : 0) - z) * g.nx * g.ny] +
+           phi[i + ((z + 1 < g.nz ? z + 1 : z) - z) * g.nx * g.ny];
+    const float inc = b * (s - 2.0f * ndim * p) + a * (p - p * p * p);
+    const float q = phat[i];
+    mabs = fmaxf(mabs, fabsf(q));
+    mres = fmaxf(mres, fabsf(q - p - nsteps * inc));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mabs = fmaxf(mabs, __shfl_xor_sync(0xffffffffu, mabs, o));
+    mres = fmaxf(mres, __shfl_xor_sync(0xffffffffu, mres, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, __float_as_uint(mabs));
+    atomicMax(out + 1, __float_as_uint(mres));
+  }
+}
+
+cudaError_t launch_guard(const float *phi, const float *phat, const GridParams &g, int ndim,
+                         int nsteps, unsigned int *out_dev, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out_dev, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  guard_kernel<<<1216, 256, 0, s>>>(phi, phat, g, ndim, (float)nsteps, out_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace ac

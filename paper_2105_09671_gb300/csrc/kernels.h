@@ -49,6 +49,11 @@ int64_t observe_noalloc_max_rows();
 cudaError_t launch_observe_noalloc(int dtype, const GridParams &g, const void *phi, double hd,
                                    double eps, double h, double *out_dev, cudaStream_t s);
 
+// Guard of a learned jump (FP32, pitch == nx): out_dev[0] = bits of
+// max |phi_hat|, out_dev[1] = bits of max |phi_hat - phi - n dt RHS(phi)|.
+cudaError_t launch_guard(const float *phi, const float *phat, const GridParams &g, int ndim,
+                         int nsteps, unsigned int *out_dev, cudaStream_t s);
+
 cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double h,
                                const double lower[3], const double center[3], double r0,
                                double eps, cudaStream_t s);

@@ -216,7 +216,8 @@ typedef struct {
 } ac_guard;
 
 int ac_net_param_count(int32_t ndim, int64_t *out);
-/* ndim 2 or 3; parameters start at zero (set them with ac_net_set_params).
+/* ndim 2 or 3; weights start He-normal (std sqrt(2 / fan_in), seed 0) with
+ * the last layer and all biases zero, i.e. the identity jump.
  * Allocates parameter, gradient and optimiser buffers; per-shape activation
  * buffers are allocated on first use of a shape and kept until destroy. */
 int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out);
@@ -224,6 +225,8 @@ int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out);
  * setting them also resets the Adam moments.  Synchronise. */
 int ac_net_set_params(ac_net *net, const float *host_params, int64_t count);
 int ac_net_get_params(ac_net *net, float *host_params, int64_t count);
+/* Re-draw the initial weights as ac_net_create does, from another seed. */
+int ac_net_init_params(ac_net *net, uint64_t seed);
 /* out = phi + scale * NN(phi) for batch fields of nx x ny x nz (nz = 1 in
  * 2D).  phi and out must not overlap.  Asynchronous. */
 int ac_net_forward(ac_net *net, const float *phi_dev, float *out_dev, int32_t batch, int64_t nx,
@@ -241,6 +244,37 @@ int ac_net_train_step(ac_net *net, const float *phi_dev, const float *target_dev
                       int64_t nx, int64_t ny, int64_t nz, double scale, double lr, double *loss);
 int ac_net_launch_count(ac_net *net, int64_t *out);
 int ac_net_destroy(ac_net *net);
+
+/* Training on trajectories of the plain stepper (the network's only data). */
+typedef struct {
+  int32_t n;                /* training grid: n x n (2D) or n^3 (3D), h = 1/n, n % 4 == 0 */
+  double eps_cells;         /* eps = eps_cells * h (dt = 0.1 h^2)                       */
+  int32_t pool;             /* trajectories advanced together = the batch size           */
+  int32_t trajectory_jumps; /* jumps after which a trajectory is replaced by a new one   */
+  int32_t iterations;       /* Adam steps                                                */
+  int32_t steps_per_jump;   /* Euler steps per jump                                      */
+  double lr, lr_final;      /* cosine learning-rate schedule from lr to lr_final         */
+  uint64_t seed;
+} ac_train_config;
+
+/* Train `net` (its ndim) on the fly: a pool of trajectories of the plain
+ * stepper, started staggered in age, each replaced after trajectory_jumps
+ * jumps by a new initial state (alternately random with amplitude 0.1 and a
+ * tanh circle / sphere of radius uniform in [0.1, 0.4], Section 3.1).  Each
+ * iteration takes the pool as inputs, its steps_per_jump-step advance by
+ * the plain stepper (the batched persistent stepper in 2D) as targets, and
+ * one Adam step.  loss_history (length iterations, may be NULL) receives
+ * each iteration's loss; *trajectories_used the number of trajectories
+ * started.  Allocates its pool for the duration of the call.  Synchronises. */
+int ac_net_train(ac_net *net, const ac_train_config *cfg, double *loss_history,
+                 int64_t *trajectories_used);
+
+/* Guard quantities of a candidate jump phat_dev (FP32 field of the context's
+ * layout, pitch_x == nx) from the context's current phi over `steps` steps:
+ * out[0] = max |phat|, out[1] = max |phat - phi - steps dt RHS(phi)| with
+ * RHS the bracket of Eq. (pytorchACeq).  Used to calibrate the residual
+ * threshold on jumps of the plain stepper.  Synchronises. */
+int ac_jump_residual(ac_ctx *ctx, const float *phat_dev, int32_t steps, double out[2]);
 
 /* Advance the context's field (FP32, pitch_x == nx, same stream as the net)
  * by `jumps` learned jumps of guard->steps_per_jump steps each.  Every jump

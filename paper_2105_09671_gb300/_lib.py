@@ -35,7 +35,8 @@ EXPORTED = (
     "ac_tc_gemm_bf16_n32",
     "ac_net_param_count", "ac_net_create", "ac_net_set_params", "ac_net_get_params",
     "ac_net_forward", "ac_net_loss_grads", "ac_net_adam", "ac_net_train_step",
-    "ac_net_launch_count", "ac_net_destroy", "ac_learned_advance",
+    "ac_net_launch_count", "ac_net_destroy", "ac_learned_advance", "ac_net_train",
+    "ac_net_init_params", "ac_jump_residual",
 )
 
 
@@ -59,6 +60,20 @@ class AcGuard(ctypes.Structure):
         ("energy_rtol", ctypes.c_double),
         ("max_abs", ctypes.c_double),
         ("residual_tol", ctypes.c_double),
+    ]
+
+
+class AcTrainConfig(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("eps_cells", ctypes.c_double),
+        ("pool", ctypes.c_int32),
+        ("trajectory_jumps", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("steps_per_jump", ctypes.c_int32),
+        ("lr", ctypes.c_double),
+        ("lr_final", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -133,6 +148,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_net_launch_count": [vp, ctypes.POINTER(i64)],
         "ac_net_destroy": [vp],
         "ac_learned_advance": [vp, vp, i64, ctypes.POINTER(AcGuard), ctypes.POINTER(i64)],
+        "ac_net_train": [vp, ctypes.POINTER(AcTrainConfig), vp, ctypes.POINTER(i64)],
+        "ac_net_init_params": [vp, u64],
+        "ac_jump_residual": [vp, vp, i32, ctypes.POINTER(dbl)],
         "ac_destroy": [vp],
     }
     for name, args in sig.items():
@@ -407,3 +425,23 @@ def ac_learned_advance(ctx: int, net: int, jumps: int, guard: "AcGuard") -> int:
     check(lib().ac_learned_advance(ctypes.c_void_p(ctx), ctypes.c_void_p(net), int(jumps),
                                    ctypes.byref(guard), ctypes.byref(fb)))
     return fb.value
+
+
+def ac_net_train(net: int, cfg: "AcTrainConfig"):
+    """Returns (loss history as a numpy array, trajectories used)."""
+    import numpy as np
+    hist = np.zeros(cfg.iterations, dtype=np.float64)
+    used = ctypes.c_int64()
+    check(lib().ac_net_train(ctypes.c_void_p(net), ctypes.byref(cfg), hist.ctypes.data_as(ctypes.c_void_p),
+                             ctypes.byref(used)))
+    return hist, used.value
+
+
+def ac_net_init_params(net: int, seed: int) -> None:
+    check(lib().ac_net_init_params(ctypes.c_void_p(net), int(seed)))
+
+
+def ac_jump_residual(ctx: int, phat_ptr: int, steps: int) -> tuple:
+    out = (ctypes.c_double * 2)()
+    check(lib().ac_jump_residual(ctypes.c_void_p(ctx), ctypes.c_void_p(phat_ptr), int(steps), out))
+    return out[0], out[1]

@@ -22,10 +22,11 @@ LIB = os.path.join(OUT_DIR, "libac.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Kernels use C++20 (templated lambdas for the unrolled streaming loops).
-# ac_batch.cu is host-only C++ that needs nothing newer than C++17, and
-# nvcc 13.0's front end aborts on it in C++20 mode (an internal assertion in
-# its standard-library destructor handling), so it is compiled as C++17.
-STD_OVERRIDE = {"ac_batch.cu": "-std=c++17"}
+# ac_batch.cu and ac_net.cu are host-only C++ that needs nothing newer than
+# C++17, and nvcc 13.0's front end aborts on them in C++20 mode (an internal
+# assertion when destroying std::vector elements of the C-linkage descriptor
+# types), so they are compiled as C++17.
+STD_OVERRIDE = {"ac_batch.cu": "-std=c++17", "ac_net.cu": "-std=c++17"}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ctx.h"
 #include "net.cuh"
@@ -116,6 +117,30 @@ static int check_shape(int ndim, int32_t batch, int64_t nx, int64_t ny, int64_t 
   return AC_OK;
 }
 
+// He-normal initial weights (std sqrt(2 / fan_in)) from a SplitMix64 stream
+// and Box-Muller; the last layer starts at zero, so the initial jump is the
+// identity; biases start at zero.
+static void he_init(const NetLayout &L, uint64_t seed, std::vector<float> &p) {
+  p.assign((size_t)L.total, 0.0f);
+  uint64_t state = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next_u = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * 0x1.0p-53;  // (0, 1)
+  };
+  for (int l = 0; l < kNetLayers - 1; ++l) {
+    const int64_t count = (int64_t)L.T * NetLayout::cin(l) * NetLayout::cout(l);
+    const double sd = std::sqrt(2.0 / ((double)L.T * NetLayout::cin(l)));
+    for (int64_t i = 0; i < count; ++i) {
+      const double u1 = next_u(), u2 = next_u();
+      p[L.w[l] + i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+    }
+  }
+}
+
 extern "C" int ac_net_param_count(int32_t ndim, int64_t *out) {
   if ((ndim != 2 && ndim != 3) || !out) return nfail(AC_ERR_INVALID, "ndim must be 2 or 3");
   *out = net_layout(ndim).total;
@@ -145,7 +170,9 @@ extern "C" int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out) {
   if (e == cudaSuccess) e = cudaMalloc(&b.loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&net->guard, 2 * sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMemset(b.params, 0, pbytes);
+  std::vector<float> init;
+  he_init(b.layout, 0, init);
+  if (e == cudaSuccess) e = cudaMemcpy(b.params, init.data(), pbytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b.m, 0, pbytes);
   if (e == cudaSuccess) e = cudaMemset(b.v, 0, pbytes);
   if (e == cudaSuccess) e = cudaMemset(b.status, 0, sizeof(int));
@@ -190,6 +217,13 @@ extern "C" int ac_net_set_params(ac_net *net, const float *host_params, int64_t 
   ++net->launches;
   NC_CUDA(cudaStreamSynchronize(net->stream));
   return AC_OK;
+}
+
+extern "C" int ac_net_init_params(ac_net *net, uint64_t seed) {
+  if (!net) return nfail(AC_ERR_INVALID, "net is NULL");
+  std::vector<float> init;
+  he_init(net->base.layout, seed, init);
+  return ac_net_set_params(net, init.data(), (int64_t)init.size());
 }
 
 extern "C" int ac_net_get_params(ac_net *net, float *host_params, int64_t count) {
@@ -277,6 +311,25 @@ extern "C" int ac_net_launch_count(ac_net *net, int64_t *out) {
 }
 
 // ------------------------------------------------------ guarded advance ----
+extern "C" int ac_jump_residual(ac_ctx *c, const float *phat_dev, int32_t steps, double out[2]) {
+  if (!c || !phat_dev || !out) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (c->d.dtype != AC_F32 || c->d.pitch_x != c->d.nx)
+    return nfail(AC_ERR_UNSUPPORTED, "needs an FP32 context with pitch_x == nx");
+  if (steps < 1) return nfail(AC_ERR_INVALID, "steps must be >= 1");
+  unsigned int *buf = reinterpret_cast<unsigned int *>(c->d_out);
+  cudaError_t e = launch_guard(static_cast<const float *>(c->phi), phat_dev, c->gp, c->d.ndim, steps, buf, c->stream);
+  if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "guard launch failed: %s", cudaGetErrorString(e));
+  ++c->launches;
+  unsigned int h[2];
+  NC_CUDA(cudaMemcpyAsync(h, buf, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  NC_CUDA(cudaStreamSynchronize(c->stream));
+  float f[2];
+  memcpy(f, h, sizeof f);
+  out[0] = f[0];
+  out[1] = f[1];
+  return AC_OK;
+}
+
 extern "C" int ac_learned_advance(ac_ctx *c, ac_net *net, int64_t jumps, const ac_guard *guard,
                                   int64_t *fallbacks) {
   if (!c || !net || !guard) return nfail(AC_ERR_INVALID, "NULL argument");
@@ -333,4 +386,157 @@ extern "C" int ac_learned_advance(ac_ctx *c, ac_net *net, int64_t jumps, const a
   }
   if (fallbacks) *fallbacks = fb;
   return AC_OK;
+}
+
+// ---------------------------------------------------------------- training --
+// Training data come from the plain stepper itself: a pool of `pool`
+// trajectories on n^d grids (h = 1/n, dt = 0.1 h^2, eps = eps_cells h),
+// staggered in age so that every phase of the dynamics is in each batch.
+// Each iteration copies the pool, advances the copy by steps_per_jump plain
+// steps (the targets), takes one Adam step on (pool, targets) and moves the
+// pool to the targets.  A trajectory older than trajectory_jumps is replaced
+// by a new one: alternately a random state (amplitude 0.1, Section 3.1) and a
+// tanh circle / sphere of radius uniform in [0.1, 0.4] centred in the domain.
+namespace {
+uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+extern "C" int ac_net_train(ac_net *net, const ac_train_config *cfg, double *loss_history,
+                            int64_t *trajectories_used) {
+  if (!net || !cfg) return nfail(AC_ERR_INVALID, "NULL argument");
+  const int nd = net->ndim, n = cfg->n, B = cfg->pool, spj = cfg->steps_per_jump;
+  if (n < 8 || n > 4096 || n % 4) return nfail(AC_ERR_INVALID, "n must be a multiple of 4 in [8, 4096]");
+  if (B < 1 || B > 4096 || cfg->iterations < 1 || spj < 1 || cfg->trajectory_jumps < 1)
+    return nfail(AC_ERR_INVALID, "pool, iterations, steps_per_jump, trajectory_jumps must be >= 1");
+  if (!(cfg->eps_cells > 0) || !(cfg->lr > 0) || !(cfg->lr_final >= 0))
+    return nfail(AC_ERR_INVALID, "eps_cells and lr must be > 0");
+  const int64_t cells = nd == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const double h = 1.0 / n, eps = cfg->eps_cells * h, dt = 0.1 * h * h;
+  const double scale = spj * dt / (eps * eps);
+  cudaStream_t s = net->stream;
+
+  float *states = nullptr, *targets = nullptr, *ws = nullptr;
+  ac_batch *batch = nullptr;
+  std::vector<ac_ctx *> ctxs;
+  int rc = AC_OK;
+  auto cleanup = [&]() {
+    if (batch) ac_batch_destroy(batch);
+    for (ac_ctx *c : ctxs) ac_destroy(c);
+    cudaFree(states);
+    cudaFree(targets);
+    cudaFree(ws);
+  };
+  const size_t fbytes = (size_t)cells * sizeof(float);
+  if (cudaMalloc(&states, fbytes * B) != cudaSuccess || cudaMalloc(&targets, fbytes * B) != cudaSuccess ||
+      cudaMalloc(&ws, (fbytes + 256) * B) != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return nfail(AC_ERR_NOMEM, "training buffers do not fit");
+  }
+  ac_grid_desc d{};
+  d.ndim = nd;
+  d.dtype = AC_F32;
+  d.nx = n;
+  d.ny = n;
+  d.nz = nd == 3 ? n : 1;
+  d.pitch_x = n;
+  d.h = h;
+  d.eps = eps;
+  d.dt = dt;
+  if (nd == 2) {
+    std::vector<ac_grid_desc> descs(B, d);
+    std::vector<void *> ptrs(B);
+    for (int i = 0; i < B; ++i) ptrs[i] = targets + (size_t)i * cells;
+    rc = ac_batch_create(descs.data(), ptrs.data(), B, ws, s, &batch);
+  } else {
+    for (int i = 0; i < B && rc == AC_OK; ++i) {
+      ac_ctx *c = nullptr;
+      rc = ac_create(&d, targets + (size_t)i * cells, reinterpret_cast<char *>(ws) + (fbytes + 256) * i / 256 * 256, s, &c);
+      if (rc == AC_OK) ctxs.push_back(c);
+    }
+  }
+  if (rc) { cleanup(); return rc; }
+
+  GridParams g{};
+  g.nx = n; g.ny = n; g.nz = d.nz; g.pitch = n;
+  g.alpha = dt / (eps * eps); g.beta = dt / (h * h); g.status = nullptr;
+  int64_t used = 0;
+  auto new_trajectory = [&](int slot) -> int {
+    float *dst = states + (size_t)slot * cells;
+    const uint64_t r = mix64(cfg->seed * 0x100000001B3ull + (uint64_t)used);
+    cudaError_t e;
+    if (used % 2 == 0) {
+      e = launch_init_random(AC_F32, g, dst, r, 0.1, s);
+    } else {
+      const double r0 = 0.1 + 0.3 * (double)(r >> 11) * 0x1.0p-53;
+      const double lo[3] = {0, 0, 0}, c3[3] = {0.5, 0.5, 0.5};
+      e = launch_init_sphere(AC_F32, g, dst, h, lo, c3, r0, eps, s);
+    }
+    ++used;
+    ++net->launches;
+    return e == cudaSuccess ? AC_OK : nfail(AC_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
+  };
+  // advance the pool (in `targets`) by `steps` plain steps
+  auto step_targets = [&](int64_t steps) -> int {
+    if (steps <= 0) return AC_OK;
+    if (batch) {
+      std::vector<int64_t> nv(B, steps);
+      return ac_batch_step(batch, nv.data());
+    }
+    for (ac_ctx *c : ctxs) {
+      int r2 = ac_step(c, steps);
+      if (r2) return r2;
+    }
+    return AC_OK;
+  };
+  // staggered start: slot i begins i * L / B jumps into its trajectory
+  std::vector<int> age(B);
+  for (int i = 0; i < B && rc == AC_OK; ++i) rc = new_trajectory(i);
+  if (rc == AC_OK && cudaMemcpyAsync(targets, states, fbytes * B, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    rc = nfail(AC_ERR_CUDA, "copy failed");
+  // different pre-advance per slot: run the plain stepper slot by slot
+  for (int i = 0; i < B && rc == AC_OK; ++i) {
+    age[i] = (int)((int64_t)i * cfg->trajectory_jumps / B);
+    if (age[i] == 0) continue;
+    ac_ctx *c = nullptr;
+    rc = ac_create(&d, targets + (size_t)i * cells, ws, s, &c);
+    if (rc == AC_OK) rc = ac_step(c, (int64_t)age[i] * spj);
+    if (c) ac_destroy(c);
+  }
+  if (rc == AC_OK && cudaMemcpyAsync(states, targets, fbytes * B, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    rc = nfail(AC_ERR_CUDA, "copy failed");
+
+  const double kPi = 3.14159265358979323846;
+  for (int it = 0; it < cfg->iterations && rc == AC_OK; ++it) {
+    if (cudaMemcpyAsync(targets, states, fbytes * B, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      rc = nfail(AC_ERR_CUDA, "copy failed");
+      break;
+    }
+    rc = step_targets(spj);
+    if (rc) break;
+    const double f = cfg->iterations > 1 ? (double)it / (cfg->iterations - 1) : 1.0;
+    const double lr = cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + std::cos(kPi * f));
+    double loss = 0.0;
+    rc = ac_net_train_step(net, states, targets, B, n, n, d.nz, scale, lr, &loss);
+    if (rc) break;
+    if (loss_history) loss_history[it] = loss;
+    if (cudaMemcpyAsync(states, targets, fbytes * B, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      rc = nfail(AC_ERR_CUDA, "copy failed");
+      break;
+    }
+    for (int i = 0; i < B && rc == AC_OK; ++i)
+      if (++age[i] >= cfg->trajectory_jumps) {
+        rc = new_trajectory(i);
+        age[i] = 0;
+      }
+  }
+  if (rc == AC_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = nfail(AC_ERR_CUDA, "training failed");
+  if (trajectories_used) *trajectories_used = used;
+  cleanup();
+  return rc;
 }

@@ -284,6 +284,99 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_learned(args, ws, rank, local):
+    """The learned form: train the 2D jump network on 256^2 plain trajectories
+    (eps = 4h), then advance a 1024^2 field 2000 steps (125 guarded jumps)
+    and compare time-to-solution and error with the plain stepper."""
+    import numpy as np
+    import torch
+    import paper_2105_09671_gb300 as ac
+    from paper_2105_09671_gb300 import _lib as L
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    s = torch.cuda.Stream(device)
+    net = L.ac_net_create(2, s.cuda_stream)
+    cfg = L.AcTrainConfig(n=256, eps_cells=4.0, pool=32, trajectory_jumps=125,
+                          iterations=args.train_iters, steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=1)
+    t0 = time.perf_counter()
+    hist, used = L.ac_net_train(net, cfg)
+    train_s = time.perf_counter() - t0
+    n, jumps = 1024, 125
+    h = 1.0 / n
+    guard = L.AcGuard(16, 1e-6, 1.0 + 1e-3, 0.0)
+    out = {}
+    for init in ("circle", "random"):
+        res = {}
+        for mode in ("plain", "learned"):
+            sim = ac.Simulation((n, n), h, 4 * h, 0.1 * h * h, dtype="f32", device=device, stream=s)
+            times = []
+            fb = 0
+            for rep in range(args.warmup + args.steps):
+                if init == "circle":
+                    sim.init_sphere(r0=0.3)
+                else:
+                    sim.init_random(seed=7)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                if mode == "learned":
+                    fb = L.ac_learned_advance(sim.ctx, net, jumps, guard)
+                else:
+                    sim.step(16 * jumps)
+                e1.record(s)
+                s.synchronize()
+                if rep >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            res[mode] = (statistics.median(times), fb, sim.to_numpy().astype(np.float64))
+            sim.close()
+        ref = res["plain"][2]
+        out[init] = {"plain_ms": res["plain"][0], "learned_ms": res["learned"][0],
+                     "speedup_vs_plain": res["plain"][0] / res["learned"][0],
+                     "fallbacks": res["learned"][1], "jumps": jumps,
+                     "rel_l2_vs_plain_fp32": float(np.linalg.norm(res["learned"][2] - ref) / np.linalg.norm(ref))}
+    # tensor-core roofline of the network forward at 1024^2
+    x = torch.rand(1, n, n, device=device) * 2 - 1
+    y = torch.empty_like(x)
+    torch.cuda.synchronize(device)
+    for _ in range(3):
+        L.ac_net_forward(net, x.data_ptr(), y.data_ptr(), 1, n, n, 1, 0.1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(10):
+        L.ac_net_forward(net, x.data_ptr(), y.data_ptr(), 1, n, n, 1, 0.1)
+    e1.record(s)
+    s.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 10
+    flops = n * n * (4 * 2 * 288 * 32 + 2 * 2 * 9 * 32)
+    peak = 1889.1
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
+    achieved = flops / (fwd_ms / 1e3) / 1e12
+    cells_updates = n * n * 16 * jumps
+    line = {
+        "metric": METRIC, "value": cells_updates / (out["circle"]["learned_ms"] / 1e3) / 1e9, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["circle"]["learned_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "learned_jump_1024_2d", "grid": [n, n], "euler_steps": 16 * jumps,
+                   "steps_per_jump": 16, "train": {"n": 256, "pool": 32, "iterations": args.train_iters,
+                                                   "trajectories": used, "seconds": train_s,
+                                                   "loss_first": float(np.median(hist[:50])),
+                                                   "loss_last": float(np.median(hist[-50:]))},
+                   "guard": {"energy_rtol": 1e-6, "max_abs": 1.001, "residual_tol": 0.0}},
+        "cases": out,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "network forward (4 tcgen05 convs + 2 CUDA-core end layers)",
+                     "forward_ms_1024": fwd_ms},
+    }
+    L.ac_net_destroy(net)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     """The oracle arm: the FP64 C oracle on the host cores, same workload."""
     if rank != 0:
@@ -446,7 +539,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sphere512",
-                    choices=["sphere512", "separation4096", "batch512"])
+                    choices=["sphere512", "separation4096", "batch512", "learned1024"])
+    ap.add_argument("--train-iters", type=int, default=1500)
     ap.add_argument("--k", type=int, default=0,
                     help="force the temporal-block depth (negative: direct kernel, k=1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -462,6 +556,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.workload == "batch512":
         run_batch(args, ws, rank, local)
+    elif args.workload == "learned1024":
+        run_learned(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -27,7 +27,11 @@ def main(argv=None):
     ap.add_argument("--eps-cells", type=float, default=1.5, help="eps in units of h")
     ap.add_argument("--init", default="sphere", choices=["sphere", "random"])
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--net", action="store_true",
+                    help="run the learned jump network forward instead of the stepper")
     args = ap.parse_args(argv)
+    if args.net:
+        return net_main(args)
 
     shape = tuple(args.shape)
     h = 1.0 / shape[-1]
@@ -64,6 +68,36 @@ def main(argv=None):
                       "gcell_updates_per_s": cells * args.steps / (best / 1e3) / 1e9,
                       "energy": energy, "status": sim.status()}))
     sim.close()
+
+
+def net_main(args):
+    """Forward passes of the jump network (He-initialised, seed 0) on a random
+    field of the given shape; prints the mean time per forward."""
+    import torch
+
+    from paper_2105_09671_gb300 import _lib as L
+
+    shape = tuple(args.shape)
+    ndim = len(shape)
+    stream = torch.cuda.Stream()
+    net = L.ac_net_create(ndim, stream.cuda_stream)
+    x = torch.rand(shape, device="cuda") * 2 - 1
+    y = torch.empty_like(x)
+    nz = shape[0] if ndim == 3 else 1
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.ac_net_forward(net, x.data_ptr(), y.data_ptr(), 1, shape[-1], shape[-2], nz, 0.1)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    cells = 1
+    for v in shape:
+        cells *= v
+    print(json.dumps({"shape": list(shape), "forward_ms": ms,
+                      "mcells_per_s": cells / (ms / 1e3) / 1e6}))
+    L.ac_net_destroy(net)
 
 
 if __name__ == "__main__":

@@ -152,7 +152,22 @@ enum {
 int ac_set_schedule(ac_ctx *ctx, int32_t variant, int32_t k);
 int ac_get_schedule(ac_ctx *ctx, int32_t *variant, int32_t *k);
 
-/* Time the candidate (variant, k) schedules on the context's own buffers
+/* Tile shape of the 3D streaming kernel (the xy block each CTA streams
+ * along z; the temporal blocking of Section 3.2 recomputes a halo of k cells
+ * around it).  Tiles 0..AC_NUM_TILES_3D-1 (FP32 storage; FP64 tiles are half
+ * as wide in x):
+ *   0: 128 x 32 outputs, 3 vectors per thread (one CTA per SM)
+ *   1: 128 x 16 outputs, several CTAs per SM
+ *   2: 128 x 32 outputs, 2 vectors per thread (more warps per CTA)
+ * AC_TILE_AUTO (-1) restores the autotuned or default choice.  2D grids
+ * accept tile 0 only (AC_ERR_UNSUPPORTED otherwise).  The result of a step
+ * does not depend on the tile. */
+#define AC_TILE_AUTO (-1)
+#define AC_NUM_TILES_3D 3
+int ac_set_tile(ac_ctx *ctx, int32_t tile);
+int ac_get_tile(ac_ctx *ctx, int32_t *tile);
+
+/* Time the candidate (variant, k, tile) schedules on the context's own buffers
  * with CUDA events (about steps_per_trial steps each) and keep the fastest.
  * phi is saved to a temporary device buffer that this call allocates and
  * frees, and restored after every trial, so the field is unchanged.  The

@@ -23,10 +23,12 @@ AC_ERR_NOMEM = 6
 AC_F64, AC_F32, AC_F16S = 0, 1, 2
 AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM = 0, 1, 2
 AC_MAX_K = 8
+AC_TILE_AUTO, AC_NUM_TILES_3D = -1, 3
 
 EXPORTED = (
     "ac_workspace_bytes", "ac_create", "ac_step", "ac_energy", "ac_phase_volume", "ac_observe",
-    "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_autotune",
+    "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_set_tile",
+    "ac_get_tile", "ac_autotune",
     "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
     "ac_last_error", "ac_version",
     "ac_batch_workspace_bytes", "ac_batch_create", "ac_batch_step", "ac_batch_set_schedule",
@@ -119,6 +121,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_init_random": [vp, u64, dbl],
         "ac_set_schedule": [vp, i32, i32],
         "ac_get_schedule": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "ac_set_tile": [vp, i32],
+        "ac_get_tile": [vp, ctypes.POINTER(i32)],
         "ac_autotune": [vp, i64],
         "ac_set_graph": [vp, i32],
         "ac_status": [vp],
@@ -235,6 +239,16 @@ def ac_get_schedule(ctx: int) -> tuple:
     v, k = ctypes.c_int32(), ctypes.c_int32()
     check(lib().ac_get_schedule(ctypes.c_void_p(ctx), ctypes.byref(v), ctypes.byref(k)))
     return v.value, k.value
+
+
+def ac_set_tile(ctx: int, tile: int) -> None:
+    check(lib().ac_set_tile(ctypes.c_void_p(ctx), int(tile)))
+
+
+def ac_get_tile(ctx: int) -> int:
+    t = ctypes.c_int32()
+    check(lib().ac_get_tile(ctypes.c_void_p(ctx), ctypes.byref(t)))
+    return t.value
 
 
 def ac_autotune(ctx: int, steps_per_trial: int = 64) -> None:

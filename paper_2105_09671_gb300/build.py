@@ -27,6 +27,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # assertion when destroying std::vector elements of the C-linkage descriptor
 # types), so they are compiled as C++17.
 STD_OVERRIDE = {"ac_batch.cu": "-std=c++17", "ac_net.cu": "-std=c++17"}
+# Sources compiled several times with different defines, one object each
+# (the 3D stencil per tile shape: its kernel instantiations then compile in
+# parallel processes).
+_S3_TILES = 3
+VARIANTS = {f"k_stream3d_{t}.cu": [f"-DAC_S3_TILE={i}" for i in range(_S3_TILES)]
+            for t in ("f64", "f32", "f16")}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
 
@@ -54,11 +60,25 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(nvcc: str, src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+def _units() -> list[tuple[str, str, list[str]]]:
+    """(source, object, extra defines) of every compilation."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        defs = VARIANTS.get(os.path.basename(src))
+        if defs is None:
+            out.append((src, os.path.join(OUT_DIR, base + ".o"), []))
+        else:
+            for i, d in enumerate(defs):
+                out.append((src, os.path.join(OUT_DIR, f"{base}_v{i}.o"), [d]))
+    return out
+
+
+def _compile(nvcc: str, unit: tuple[str, str, list[str]], verbose_ptxas: bool) -> str:
+    src, obj, defs = unit
     flags = [STD_OVERRIDE.get(os.path.basename(src), f) if f.startswith("-std=") else f
              for f in NVCC_FLAGS]
-    cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
+    cmd = [nvcc, *ARCH, *flags, *defs, "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -75,9 +95,11 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(nvcc, s, verbose_ptxas), srcs))
+    units = _units()
+    # longest compilations first (the stencil kernels), so they start at once
+    units.sort(key=lambda u: ("stream" not in u[0] and "batch" not in u[0] and "net" not in u[0], u[1]))
+    with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda u: _compile(nvcc, u, verbose_ptxas), units))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

@@ -22,6 +22,7 @@ def main(argv=None):
     ap.add_argument("--shape", type=int, nargs="+", required=True, help="ny nx or nz ny nx")
     ap.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16s"])
     ap.add_argument("--k", type=int, default=0, help="temporal depth; -1 = direct kernel; 0 = default")
+    ap.add_argument("--tile", type=int, default=-1, help="3D streaming tile; -1 = default")
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--eps-cells", type=float, default=1.5, help="eps in units of h")
@@ -43,6 +44,8 @@ def main(argv=None):
         sim.set_schedule(ac.AC_VARIANT_STREAM, args.k)
     elif args.k < 0:
         sim.set_schedule(ac.AC_VARIANT_DIRECT, 1)
+    if args.tile >= 0:
+        sim.set_tile(args.tile)
     if args.init == "sphere":
         sim.init_sphere(r0=0.25)
     else:
@@ -50,6 +53,7 @@ def main(argv=None):
     if args.autotune:
         sim.autotune()
     v, k = sim.schedule()
+    tile = sim.tile()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
     for _ in range(args.repeat):
@@ -63,7 +67,7 @@ def main(argv=None):
     for s in shape:
         cells *= s
     best = min(times)
-    print(json.dumps({"shape": list(shape), "dtype": args.dtype, "variant": v, "k": k,
+    print(json.dumps({"shape": list(shape), "dtype": args.dtype, "variant": v, "k": k, "tile": tile,
                       "steps": args.steps, "ms": best,
                       "gcell_updates_per_s": cells * args.steps / (best / 1e3) / 1e9,
                       "energy": energy, "status": sim.status()}))

@@ -105,7 +105,7 @@ extern "C" int ac_workspace_bytes(const ac_grid_desc *desc, size_t *out) {
   return AC_OK;
 }
 
-static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) {
+static int encode_map(ac_ctx *c, void *base, int kind, int k, int tile, CUtensorMap *out) {
   EncodeTiledFn fn = ac_encode_fn();
   if (!fn) return fail(AC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
   const ac_grid_desc &d = c->d;
@@ -119,7 +119,7 @@ static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) 
     box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
     rank = 2;
   } else {
-    Stream3DGeom gm = stream3d_geom(d.dtype, k);
+    Stream3DGeom gm = stream3d_geom(d.dtype, k, tile);
     box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
     rank = 3;
   }
@@ -130,13 +130,13 @@ static int encode_map(ac_ctx *c, void *base, int kind, int k, CUtensorMap *out) 
   return AC_OK;
 }
 
-static int ensure_maps(ac_ctx *c, int k) {
-  MapPair &m = c->maps[k];
+static int ensure_maps(ac_ctx *c, int k, int tile) {
+  MapPair &m = c->maps[tile][k];
   if (m.valid) return AC_OK;
   const int kind = c->d.ndim;
-  int rc = encode_map(c, c->phi, kind, k, &m.phi);
+  int rc = encode_map(c, c->phi, kind, k, tile, &m.phi);
   if (rc) return rc;
-  rc = encode_map(c, c->ws, kind, k, &m.ws);
+  rc = encode_map(c, c->ws, kind, k, tile, &m.ws);
   if (rc) return rc;
   m.valid = true;
   return AC_OK;
@@ -211,10 +211,11 @@ extern "C" int ac_destroy(ac_ctx *c) {
 }
 
 // ------------------------------------------------------------- schedules --
-static bool schedule_ok(const ac_ctx *c, int variant, int k) {
+static bool schedule_ok(const ac_ctx *c, int variant, int k, int tile = 0) {
   if (variant == AC_VARIANT_DIRECT) return k == 1;
   if (variant == AC_VARIANT_STREAM)
-    return c->d.ndim == 2 ? stream2d_supported(c->d.dtype, k) : stream3d_supported(c->d.dtype, k);
+    return c->d.ndim == 2 ? tile == 0 && stream2d_supported(c->d.dtype, k)
+                          : stream3d_supported(c->d.dtype, k, tile);
   return false;
 }
 
@@ -239,6 +240,25 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
   default_schedule(c, variant, k);
 }
 
+// Default 3D tile per depth, measured on GB300 (512^3 FP32 / FP16, 256^3
+// FP64): k = 1 gains from several CTAs per SM (tile 1; FP64 from more warps,
+// tile 2), k = 2 from more warps per CTA (tile 2), k = 3 keeps tile 0 (the
+// others spill registers).
+static int default_tile(const ac_ctx *c, int k) {
+  if (c->d.dtype == AC_F64) return k == 1 ? 2 : 0;
+  return k == 1 ? 1 : k == 2 ? 2 : 0;
+}
+
+// The tile of a streaming launch: the user's, else the autotuner's (when it
+// is available at this depth), else the default.
+static int effective_tile(const ac_ctx *c, int variant, int k) {
+  if (variant != AC_VARIANT_STREAM || c->d.ndim != 3) return 0;
+  if (c->tile != AC_TILE_AUTO && schedule_ok(c, variant, k, c->tile)) return c->tile;
+  if (c->tuned_variant && schedule_ok(c, variant, k, c->tuned_tile)) return c->tuned_tile;
+  const int t = default_tile(c, k);
+  return schedule_ok(c, variant, k, t) ? t : 0;
+}
+
 extern "C" int ac_set_schedule(ac_ctx *c, int32_t variant, int32_t k) {
   if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
   if (variant == AC_VARIANT_AUTO && k == 0) {
@@ -254,6 +274,23 @@ extern "C" int ac_set_schedule(ac_ctx *c, int32_t variant, int32_t k) {
                 variant, k, c->d.ndim, c->d.dtype);
   c->variant = variant;
   c->k = k;
+  return AC_OK;
+}
+
+extern "C" int ac_set_tile(ac_ctx *c, int32_t tile) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (tile == AC_TILE_AUTO) { c->tile = AC_TILE_AUTO; return AC_OK; }
+  if (tile < 0 || tile >= AC_NUM_TILES_3D) return fail(AC_ERR_INVALID, "tile must be in 0..%d", AC_NUM_TILES_3D - 1);
+  if (c->d.ndim == 2 && tile != 0) return fail(AC_ERR_UNSUPPORTED, "2D grids have tile 0 only");
+  c->tile = tile;
+  return AC_OK;
+}
+
+extern "C" int ac_get_tile(ac_ctx *c, int32_t *tile) {
+  if (!c || !tile) return fail(AC_ERR_INVALID, "NULL argument");
+  int v, kk;
+  effective_schedule(c, &v, &kk);
+  *tile = effective_tile(c, v, kk);
   return AC_OK;
 }
 
@@ -287,7 +324,7 @@ bool ac_plan_depths(int64_t n, int k, std::vector<int> &depths) {
   return false;
 }
 
-static int issue_steps(ac_ctx *c, int64_t n, int variant, int k) {
+static int issue_steps(ac_ctx *c, int64_t n, int variant, int k, int tile) {
   std::vector<int> depths;
   const bool even = variant == AC_VARIANT_DIRECT ? (n % 2 == 0) : ac_plan_depths(n, k, depths);
   if (variant == AC_VARIANT_DIRECT) depths.assign((size_t)n, 1);
@@ -299,11 +336,13 @@ static int issue_steps(ac_ctx *c, int64_t n, int variant, int k) {
     if (variant == AC_VARIANT_DIRECT) {
       e = launch_direct(c->d.ndim, c->d.dtype, c->gp, src, dst, c->stream);
     } else {
-      int rc = ensure_maps(c, dep);
+      // a remainder depth the tile does not offer runs on tile 0
+      const int tl = schedule_ok(c, variant, dep, tile) ? tile : 0;
+      int rc = ensure_maps(c, dep, tl);
       if (rc) return rc;
-      const CUtensorMap *m = src_is_phi ? &c->maps[dep].phi : &c->maps[dep].ws;
+      const CUtensorMap *m = src_is_phi ? &c->maps[tl][dep].phi : &c->maps[tl][dep].ws;
       e = c->d.ndim == 2 ? launch_stream2d(c->d.dtype, dep, c->gp, m, dst, c->num_sms, c->stream)
-                         : launch_stream3d(c->d.dtype, dep, c->gp, m, dst, c->num_sms, c->stream);
+                         : launch_stream3d(c->d.dtype, dep, tl, c->gp, m, dst, c->num_sms, c->stream);
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stencil launch failed: %s", cudaGetErrorString(e));
     ++c->launches;
@@ -323,14 +362,15 @@ extern "C" int ac_step(ac_ctx *c, int64_t n) {
   if (n == 0) return AC_OK;
   int variant, k;
   effective_schedule(c, &variant, &k);
-  if (!c->use_graph || c->stream == nullptr) return issue_steps(c, n, variant, k);
+  const int tile = effective_tile(c, variant, k);
+  if (!c->use_graph || c->stream == nullptr) return issue_steps(c, n, variant, k, tile);
   // graph replay: capture the launch sequence for this (n, schedule) once
   if (c->graph_exec == nullptr || c->graph_n != n || c->graph_variant != variant ||
-      c->graph_k != k) {
+      c->graph_k != k || c->graph_tile != tile) {
     release_graph(c);
     AC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
     const int64_t before = c->launches;
-    int rc = issue_steps(c, n, variant, k);
+    int rc = issue_steps(c, n, variant, k, tile);
     c->graph_launches = c->launches - before;
     c->launches = before;
     cudaGraph_t graph = nullptr;
@@ -343,6 +383,7 @@ extern "C" int ac_step(ac_ctx *c, int64_t n) {
     c->graph_n = n;
     c->graph_variant = variant;
     c->graph_k = k;
+    c->graph_tile = tile;
   }
   AC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
   c->launches += c->graph_launches;
@@ -437,7 +478,10 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+  int variant, k, tile;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static int size_class(const ac_grid_desc &d) {
@@ -453,16 +497,18 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      c->tuned_variant = it->second.first;
-      c->tuned_k = it->second.second;
+      c->tuned_variant = it->second.variant;
+      c->tuned_k = it->second.k;
+      c->tuned_tile = it->second.tile;
       return AC_OK;
     }
   }
-  // candidates: the direct kernel and every streaming depth
-  std::vector<std::pair<int, int>> cand;
-  cand.push_back({AC_VARIANT_DIRECT, 1});
+  // candidates: the direct kernel and every streaming depth and tile
+  std::vector<TuneChoice> cand;
+  cand.push_back({AC_VARIANT_DIRECT, 1, 0});
   for (int k = 1; k <= AC_MAX_K; ++k)
-    if (schedule_ok(c, AC_VARIANT_STREAM, k)) cand.push_back({AC_VARIANT_STREAM, k});
+    for (int tile = 0; tile < (c->d.ndim == 3 ? AC_NUM_TILES_3D : 1); ++tile)
+      if (schedule_ok(c, AC_VARIANT_STREAM, k, tile)) cand.push_back({AC_VARIANT_STREAM, k, tile});
   const size_t bytes = field_bytes(&c->d);
   void *backup = nullptr;
   AC_CUDA(cudaMalloc(&backup, bytes));
@@ -471,15 +517,15 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   cudaEventCreate(&e1);
   int rc = AC_OK;
   float best = 1e30f;
-  std::pair<int, int> best_c = cand.front();
+  TuneChoice best_c = cand.front();
   cudaMemcpyAsync(backup, c->phi, bytes, cudaMemcpyDeviceToDevice, c->stream);
   for (auto &cd : cand) {
     // steps rounded to a multiple of 2k so every candidate runs full passes
-    const int64_t n = std::max<int64_t>(2 * cd.second, steps_per_trial / (2 * cd.second) * (2 * cd.second));
-    rc = issue_steps(c, 2 * cd.second, cd.first, cd.second);  // warm-up
+    const int64_t n = std::max<int64_t>(2 * cd.k, steps_per_trial / (2 * cd.k) * (2 * cd.k));
+    rc = issue_steps(c, 2 * cd.k, cd.variant, cd.k, cd.tile);  // warm-up
     if (rc) break;
     cudaEventRecord(e0, c->stream);
-    rc = issue_steps(c, n, cd.first, cd.second);
+    rc = issue_steps(c, n, cd.variant, cd.k, cd.tile);
     if (rc) break;
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
@@ -494,8 +540,9 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   cudaEventDestroy(e1);
   cudaFree(backup);
   if (rc) return rc;
-  c->tuned_variant = best_c.first;
-  c->tuned_k = best_c.second;
+  c->tuned_variant = best_c.variant;
+  c->tuned_k = best_c.k;
+  c->tuned_tile = best_c.tile;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best_c;
   return AC_OK;

@@ -22,8 +22,8 @@ struct Stream3DGeom {
 
 bool stream2d_supported(int dtype, int k);
 Stream2DGeom stream2d_geom(int dtype, int k);
-bool stream3d_supported(int dtype, int k);
-Stream3DGeom stream3d_geom(int dtype, int k);
+bool stream3d_supported(int dtype, int k, int tile);
+Stream3DGeom stream3d_geom(int dtype, int k, int tile);
 
 // One step per launch, clamped global-memory neighbours (2D and 3D).
 cudaError_t launch_direct(int ndim, int dtype, const GridParams &g, const void *src, void *dst,
@@ -32,8 +32,8 @@ cudaError_t launch_direct(int ndim, int dtype, const GridParams &g, const void *
 // stream{2,3}d_geom(dtype, k).
 cudaError_t launch_stream2d(int dtype, int k, const GridParams &g, const CUtensorMap *src_map,
                             void *dst, int num_sms, cudaStream_t s);
-cudaError_t launch_stream3d(int dtype, int k, const GridParams &g, const CUtensorMap *src_map,
-                            void *dst, int num_sms, cudaStream_t s);
+cudaError_t launch_stream3d(int dtype, int k, int tile, const GridParams &g,
+                            const CUtensorMap *src_map, void *dst, int num_sms, cudaStream_t s);
 
 // FP64 reductions: out[0] = sum F(phi), out[1] = sum over interior faces of
 // (phi_a - phi_b)^2, out[2] = sum (1 + phi)/2, out[3] = non-finite count.

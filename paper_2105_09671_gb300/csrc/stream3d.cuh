@@ -33,14 +33,24 @@
 
 namespace ac {
 
-template <typename T> struct S3Cfg;
-template <> struct S3Cfg<float> { static constexpr int OX = 128, OY = 32, VPT = 3, D = 4, KMAX = 3; };
-template <> struct S3Cfg<double> { static constexpr int OX = 64, OY = 32, VPT = 3, D = 4, KMAX = 2; };
-template <> struct S3Cfg<__half> { static constexpr int OX = 128, OY = 32, VPT = 2, D = 4, KMAX = 3; };
+// Tile shapes (the autotuner picks one): TILE 0 = 32 output rows, the default
+// vectors per thread; TILE 1 = 16 output rows (several CTAs per SM, each with
+// its own barrier); TILE 2 = 32 rows with two vectors per thread (more warps).
+constexpr int kS3Tiles = 3;
+template <typename T, int TILE> struct S3Cfg;
+template <int TILE> struct S3Cfg<float, TILE> {
+  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 2 : 3, D = 4, KMAX = 3;
+};
+template <int TILE> struct S3Cfg<double, TILE> {
+  static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 2 : 3, D = 4, KMAX = 2;
+};
+template <int TILE> struct S3Cfg<__half, TILE> {
+  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 1 : 2, D = 4, KMAX = 3;
+};
 
-template <typename T, int K>
+template <typename T, int K, int TILE = 0>
 struct S3Geom {
-  using Cfg = S3Cfg<T>;
+  using Cfg = S3Cfg<T, TILE>;
   using C = typename Traits<T>::C;
   static constexpr int V = Traits<T>::V;
   static constexpr int HX = V * ((K + V - 1) / V);
@@ -50,6 +60,7 @@ struct S3Geom {
   static constexpr int VPT = Cfg::VPT;
   static constexpr int NT = ((NVEC + VPT - 1) / VPT + 31) / 32 * 32;
   static constexpr int D = Cfg::D;
+  static constexpr int MINB = TILE == 1 ? 2 : 1;  // resident CTAs the register budget targets
   static constexpr int STAGE_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
   static constexpr int LVL_BYTES = TX * TY * (int)sizeof(C);
@@ -92,11 +103,11 @@ __device__ __forceinline__ void st_vec_c(double *buf, int idx, const double *in)
     *reinterpret_cast<double2 *>(buf + idx + i) = make_double2(in[i], in[i + 1]);
 }
 
-template <typename T, int K, bool FASTX>
-__global__ void __launch_bounds__(S3Geom<T, K>::NT, 1)
+template <typename T, int K, bool FASTX, int TILE>
+__global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MINB)
     stream3d_k(const __grid_constant__ CUtensorMap src_map, T *__restrict__ dst, GridParams g,
                int tiles_x, int tiles_y, int nzc, int zchunk) {
-  using Gm = S3Geom<T, K>;
+  using Gm = S3Geom<T, K, TILE>;
   using C = typename Traits<T>::C;
   constexpr int V = Gm::V, VPT = Gm::VPT, TXV = Gm::TXV, TY = Gm::TY, TX = Gm::TX, D = Gm::D;
   constexpr int NT = Gm::NT, NVEC = Gm::NVEC;
@@ -327,26 +338,26 @@ __global__ void __launch_bounds__(S3Geom<T, K>::NT, 1)
 
 // ------------------------------------------------------------------ host ---
 
-template <typename T, int K>
+template <typename T, int K, int TILE>
 inline Stream3DGeom s3_geom_t() {
-  using Gm = S3Geom<T, K>;
+  using Gm = S3Geom<T, K, TILE>;
   return Stream3DGeom{Gm::TX, Gm::TY, Gm::HX, Gm::OX, Gm::OY, Gm::NT, Gm::SMEM};
 }
 
-template <typename T, int K, bool FASTX>
+template <typename T, int K, bool FASTX, int TILE>
 static cudaError_t s3_launch_t(const GridParams &g, const CUtensorMap *map, void *dst, int num_sms,
                                cudaStream_t s) {
-  using Gm = S3Geom<T, K>;
+  using Gm = S3Geom<T, K, TILE>;
   int dev = 0;
   cudaGetDevice(&dev);
   static unsigned attr_mask = 0;
   static int occ_cache[32] = {0};
   if (dev < 32 && !(attr_mask & (1u << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(stream3d_k<T, K, FASTX>,
+    cudaError_t e = cudaFuncSetAttribute(stream3d_k<T, K, FASTX, TILE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream3d_k<T, K, FASTX>, Gm::NT, Gm::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream3d_k<T, K, FASTX, TILE>, Gm::NT, Gm::SMEM);
     if (e != cudaSuccess) return e;
     occ_cache[dev] = std::max(1, occ);
     attr_mask |= 1u << dev;
@@ -372,51 +383,63 @@ static cudaError_t s3_launch_t(const GridParams &g, const CUtensorMap *map, void
   const int nzc = (int)((g.nz + zchunk - 1) / zchunk);
   const int64_t items = tiles * nzc;
   const unsigned blocks = (unsigned)std::min<int64_t>(items, slots);
-  stream3d_k<T, K, FASTX><<<blocks, Gm::NT, Gm::SMEM, s>>>(*map, (T *)dst, g, tiles_x, tiles_y,
+  stream3d_k<T, K, FASTX, TILE><<<blocks, Gm::NT, Gm::SMEM, s>>>(*map, (T *)dst, g, tiles_x, tiles_y,
                                                            nzc, zchunk);
   return cudaGetLastError();
 }
 
-// Dispatch over the supported depths of one storage type.
-template <typename T>
-cudaError_t s3_dispatch(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms,
-                        cudaStream_t s) {
+// Dispatch over the supported depths and tiles of one storage type.
+template <typename T, int TILE>
+cudaError_t s3_dispatch_tile(int k, const GridParams &g, const CUtensorMap *map, void *dst,
+                             int num_sms, cudaStream_t s) {
   const bool fastx = g.nx % Traits<T>::V == 0;
   switch (k) {
     case 1:
-      return fastx ? s3_launch_t<T, 1, true>(g, map, dst, num_sms, s)
-                   : s3_launch_t<T, 1, false>(g, map, dst, num_sms, s);
+      return fastx ? s3_launch_t<T, 1, true, TILE>(g, map, dst, num_sms, s)
+                   : s3_launch_t<T, 1, false, TILE>(g, map, dst, num_sms, s);
     case 2:
-      if constexpr (S3Cfg<T>::KMAX >= 2)
-        return fastx ? s3_launch_t<T, 2, true>(g, map, dst, num_sms, s)
-                     : s3_launch_t<T, 2, false>(g, map, dst, num_sms, s);
+      if constexpr (S3Cfg<T, TILE>::KMAX >= 2)
+        return fastx ? s3_launch_t<T, 2, true, TILE>(g, map, dst, num_sms, s)
+                     : s3_launch_t<T, 2, false, TILE>(g, map, dst, num_sms, s);
       break;
     case 3:
-      if constexpr (S3Cfg<T>::KMAX >= 3)
-        return fastx ? s3_launch_t<T, 3, true>(g, map, dst, num_sms, s)
-                     : s3_launch_t<T, 3, false>(g, map, dst, num_sms, s);
+      if constexpr (S3Cfg<T, TILE>::KMAX >= 3)
+        return fastx ? s3_launch_t<T, 3, true, TILE>(g, map, dst, num_sms, s)
+                     : s3_launch_t<T, 3, false, TILE>(g, map, dst, num_sms, s);
       break;
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
-Stream3DGeom s3_geom(int k) {
+template <typename T, int TILE>
+Stream3DGeom s3_geom_tile(int k) {
   switch (k) {
-    case 1: return s3_geom_t<T, 1>();
+    case 1: return s3_geom_t<T, 1, TILE>();
     case 2:
-      if constexpr (S3Cfg<T>::KMAX >= 2) return s3_geom_t<T, 2>();
+      if constexpr (S3Cfg<T, TILE>::KMAX >= 2) return s3_geom_t<T, 2, TILE>();
       break;
     case 3:
-      if constexpr (S3Cfg<T>::KMAX >= 3) return s3_geom_t<T, 3>();
+      if constexpr (S3Cfg<T, TILE>::KMAX >= 3) return s3_geom_t<T, 3, TILE>();
       break;
   }
   return Stream3DGeom{0, 0, 0, 0, 0, 0, 0};
 }
 
-// Per-storage-type entry points (one translation unit each).
-cudaError_t stream3d_launch_f64(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
-cudaError_t stream3d_launch_f32(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
-cudaError_t stream3d_launch_f16(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
+template <typename T>
+Stream3DGeom s3_geom(int k, int tile) {
+  switch (tile) {
+    case 0: return s3_geom_tile<T, 0>(k);
+    case 1: return s3_geom_tile<T, 1>(k);
+    case 2: return s3_geom_tile<T, 2>(k);
+  }
+  return Stream3DGeom{0, 0, 0, 0, 0, 0, 0};
+}
+
+// Launch of one (storage type, tile): defined and explicitly instantiated in
+// k_stream3d_<type>.cu, which is compiled once per tile (AC_S3_TILE) so that
+// the kernel instantiations spread over parallel compiler processes.
+template <typename T, int TILE>
+cudaError_t stream3d_launch_tile(int k, const GridParams &g, const CUtensorMap *map, void *dst,
+                                 int num_sms, cudaStream_t s);
 
 }  // namespace ac

@@ -111,6 +111,13 @@ class Simulation:
     def schedule(self):
         return L.ac_get_schedule(self.ctx)
 
+    def set_tile(self, tile: int) -> None:
+        """3D streaming tile shape (0..AC_NUM_TILES_3D-1, or -1 for auto)."""
+        L.ac_set_tile(self.ctx, tile)
+
+    def tile(self) -> int:
+        return L.ac_get_tile(self.ctx)
+
     def autotune(self, steps_per_trial: int = 64) -> None:
         L.ac_autotune(self.ctx, steps_per_trial)
 

@@ -16,12 +16,14 @@ TOL_RELL2_F16S = 1e-3
 
 
 def schedules(ndim: int, dtype: str):
-    """Every (variant, k) the library accepts for this grid kind."""
+    """Every (variant, k, tile) the library accepts for this grid kind."""
     from paper_2105_09671_gb300 import _lib as L
-    out = [(L.AC_VARIANT_DIRECT, 1)]
+    out = [(L.AC_VARIANT_DIRECT, 1, 0)]
     kmax = {(2, "f64"): 8, (2, "f32"): 8, (2, "f16s"): 6, (3, "f64"): 2, (3, "f32"): 3, (3, "f16s"): 3}
+    tiles = L.AC_NUM_TILES_3D if ndim == 3 else 1
     for k in range(1, kmax[(ndim, dtype)] + 1):
-        out.append((L.AC_VARIANT_STREAM, k))
+        for tile in range(tiles):
+            out.append((L.AC_VARIANT_STREAM, k, tile))
     return out
 
 
@@ -30,12 +32,14 @@ def stored(phi0: np.ndarray, dtype: str) -> np.ndarray:
     return phi0.astype(NP[dtype]).astype(np.float64)
 
 
-def gpu_run(phi0, h, eps, dt, n, dtype, variant=None, k=None, pitch_x=None):
+def gpu_run(phi0, h, eps, dt, n, dtype, variant=None, k=None, tile=None, pitch_x=None):
     sim = ac.Simulation(phi0.shape, h, eps, dt, dtype=dtype, pitch_x=pitch_x)
     try:
         sim.load(phi0)
         if variant is not None:
             sim.set_schedule(variant, k)
+        if tile is not None:
+            sim.set_tile(tile)
         sim.step(n)
         assert sim.status() == ac.AC_OK
         return sim.to_numpy().astype(np.float64)

@@ -33,9 +33,9 @@ def test_circle64_1000_steps_every_schedule(dtype):
     w = wl.CIRCLE_64
     phi0 = oracle.init_sphere(w.shape, w.h, w.r0, w.eps)
     ref = oracle_run(phi0, w.h, w.eps, w.dt, w.steps, dtype)
-    for variant, k in schedules(2, dtype):
-        out = gpu_run(phi0, w.h, w.eps, w.dt, w.steps, dtype, variant, k)
-        assert_parity(out, ref, dtype, f"{dtype} variant {variant} k {k}")
+    for variant, k, tile in schedules(2, dtype):
+        out = gpu_run(phi0, w.h, w.eps, w.dt, w.steps, dtype, variant, k, tile)
+        assert_parity(out, ref, dtype, f"{dtype} variant {variant} k {k} tile {tile}")
 
 
 def test_default_schedule_and_graph_replay_match():
@@ -67,11 +67,11 @@ SHAPES_3D = [(1, 1, 1), (2, 3, 5), (9, 17, 33), (5, 40, 150), (33, 36, 131)]
 def test_ragged_shapes_every_schedule(shape, dtype):
     h, eps, dt = _params(shape)
     phi0 = wl.smooth_field(shape, seed=sum(shape)) + 0.05 * wl.random_field(shape, seed=7)
-    for variant, k in schedules(len(shape), dtype):
+    for variant, k, tile in schedules(len(shape), dtype):
         for n in (1, k + 2, 2 * k + 1):
             ref = oracle_run(phi0, h, eps, dt, n, dtype)
-            out = gpu_run(phi0, h, eps, dt, n, dtype, variant, k)
-            assert_parity(out, ref, dtype, f"{shape} {dtype} v{variant} k{k} n{n}")
+            out = gpu_run(phi0, h, eps, dt, n, dtype, variant, k, tile)
+            assert_parity(out, ref, dtype, f"{shape} {dtype} v{variant} k{k} t{tile} n{n}")
 
 
 @pytest.mark.parametrize("shape", [(37, 45), (7, 19, 23)])
@@ -79,8 +79,8 @@ def test_f16_storage_ragged(shape):
     h, eps, dt = _params(shape)
     phi0 = wl.smooth_field(shape, seed=3)
     ref = oracle_run(phi0, h, eps, dt, 40, "f16s")
-    for variant, k in schedules(len(shape), "f16s"):
-        out = gpu_run(phi0, h, eps, dt, 40, "f16s", variant, k)
+    for variant, k, tile in schedules(len(shape), "f16s"):
+        out = gpu_run(phi0, h, eps, dt, 40, "f16s", variant, k, tile)
         assert_parity(out, ref, "f16s", f"{shape} v{variant} k{k}")
 
 
@@ -92,9 +92,11 @@ def test_padding_never_read_or_written(shape, dtype):
     nx = shape[-1]
     es = {"f64": 8, "f32": 4, "f16s": 2}[dtype]
     pitch = -(-(nx + 19) // (16 // es)) * (16 // es)
-    for variant, k in schedules(len(shape), dtype):
+    for variant, k, tile in schedules(len(shape), dtype):
         sim = ac.Simulation(shape, h, eps, dt, dtype=dtype, pitch_x=pitch)
         try:
+            sim.set_schedule(variant, k)
+            sim.set_tile(tile)
             sim.padded.fill_(float("nan"))
             sim._ws.fill_(float("nan"))
             sim.load(phi0)
@@ -107,7 +109,7 @@ def test_padding_never_read_or_written(shape, dtype):
             sim.close()
         ref = oracle_run(phi0, h, eps, dt, 2 * k + 1, dtype)
         assert np.isfinite(out).all(), "padding leaked into the field"
-        assert_parity(out, ref, dtype, f"padded v{variant} k{k}")
+        assert_parity(out, ref, dtype, f"padded v{variant} k{k} t{tile}")
 
 
 # -------------------------------------------------- paper-fixed behaviour --
@@ -126,8 +128,8 @@ def test_hand_worked_cases_on_gpu():
             expect[...] = case["expect_all"]
         for key, val in case.get("expect", {}).items():
             expect[tuple(reversed(json.loads(key)))] = val
-        for variant, k in schedules(len(shape), "f64"):
-            out = gpu_run(phi, g["h"], g["eps"], g["dt"], 1, "f64", variant, k)
+        for variant, k, tile in schedules(len(shape), "f64"):
+            out = gpu_run(phi, g["h"], g["eps"], g["dt"], 1, "f64", variant, k, tile)
             np.testing.assert_allclose(out, expect, rtol=0, atol=1e-15, err_msg=case["name"])
 
 
@@ -137,9 +139,9 @@ def test_fixed_points_bitwise_on_gpu(shape, dtype):
     h, eps, dt = _params(shape)
     for value in (1.0, -1.0, 0.0):
         phi0 = np.full(shape, value)
-        for variant, k in schedules(len(shape), dtype):
-            out = gpu_run(phi0, h, eps, dt, 2 * k + 3, dtype, variant, k)
-            assert np.array_equal(out, phi0), f"value {value} v{variant} k{k}"
+        for variant, k, tile in schedules(len(shape), dtype):
+            out = gpu_run(phi0, h, eps, dt, 2 * k + 3, dtype, variant, k, tile)
+            assert np.array_equal(out, phi0), f"value {value} v{variant} k{k} t{tile}"
 
 
 def test_mirror_symmetry_on_gpu_fp64():
@@ -147,12 +149,53 @@ def test_mirror_symmetry_on_gpu_fp64():
     shape = (48, 48)
     h, eps, dt = _params(shape)
     phi0 = wl.random_field(shape, seed=9)
-    for variant, k in schedules(2, "f64"):
-        a = gpu_run(phi0, h, eps, dt, 12, "f64", variant, k)
-        b = gpu_run(phi0[:, ::-1].copy(), h, eps, dt, 12, "f64", variant, k)
-        c = gpu_run(phi0.T.copy(), h, eps, dt, 12, "f64", variant, k)
+    for variant, k, tile in schedules(2, "f64"):
+        a = gpu_run(phi0, h, eps, dt, 12, "f64", variant, k, tile)
+        b = gpu_run(phi0[:, ::-1].copy(), h, eps, dt, 12, "f64", variant, k, tile)
+        c = gpu_run(phi0.T.copy(), h, eps, dt, 12, "f64", variant, k, tile)
         assert np.array_equal(a[:, ::-1], b)
         assert np.array_equal(a.T, c)
+
+
+def test_mirror_symmetry_3d_every_tile():
+    # x/y/z mirrors and the x<->y swap of a cube commute with every 3D
+    # schedule and tile bit for bit (paired neighbour sums)
+    shape = (12, 40, 40)
+    h, eps, dt = _params(shape)
+    phi0 = wl.random_field(shape, seed=4)
+    for variant, k, tile in schedules(3, "f32"):
+        a = gpu_run(phi0, h, eps, dt, 2 * k + 1, "f32", variant, k, tile)
+        for f, inv in ((lambda x: x[:, :, ::-1], lambda x: x[:, :, ::-1]),
+                       (lambda x: x[:, ::-1, :], lambda x: x[:, ::-1, :]),
+                       (lambda x: x[::-1], lambda x: x[::-1]),
+                       (lambda x: x.transpose(0, 2, 1), lambda x: x.transpose(0, 2, 1))):
+            b = gpu_run(np.ascontiguousarray(f(phi0)), h, eps, dt, 2 * k + 1, "f32", variant, k, tile)
+            assert np.array_equal(inv(b), a), f"v{variant} k{k} t{tile}"
+
+
+def test_tile_selection_api():
+    sim2 = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
+    sim3 = ac.Simulation((8, 16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
+    try:
+        assert sim2.tile() == 0
+        sim2.set_tile(0)
+        with pytest.raises(ac.AcError) as e:
+            sim2.set_tile(1)
+        assert e.value.code == ac.AC_ERR_UNSUPPORTED
+        with pytest.raises(ac.AcError) as e:
+            sim3.set_tile(ac.AC_NUM_TILES_3D)
+        assert e.value.code == ac.AC_ERR_INVALID
+        for t in range(ac.AC_NUM_TILES_3D):
+            sim3.set_tile(t)
+            assert sim3.tile() == t
+        sim3.set_schedule(ac.AC_VARIANT_DIRECT, 1)
+        assert sim3.tile() == 0      # the direct kernel has no tiles
+        sim3.set_schedule(ac.AC_VARIANT_AUTO, 0)
+        sim3.set_tile(ac.AC_TILE_AUTO)
+        assert sim3.tile() in range(ac.AC_NUM_TILES_3D)
+    finally:
+        sim2.close()
+        sim3.close()
 
 
 def test_fp16_error_report_against_fp64():
@@ -162,8 +205,8 @@ def test_fp16_error_report_against_fp64():
     phi0 = oracle.init_sphere(w.shape, w.h, w.r0, w.eps)
     ref = oracle.step(phi0, w.h, w.eps, w.dt, w.steps)
     errs = {}
-    for variant, k in schedules(2, "f16s"):
-        out = gpu_run(phi0, w.h, w.eps, w.dt, w.steps, "f16s", variant, k)
+    for variant, k, tile in schedules(2, "f16s"):
+        out = gpu_run(phi0, w.h, w.eps, w.dt, w.steps, "f16s", variant, k, tile)
         errs[(variant, k)] = (rel_l2(out, ref), float(np.max(np.abs(out - ref))))
         assert errs[(variant, k)][0] <= 1e-3
     assert errs[(2, 6)][0] <= errs[(2, 1)][0] * 1.05

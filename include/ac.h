@@ -154,11 +154,11 @@ int ac_get_schedule(ac_ctx *ctx, int32_t *variant, int32_t *k);
 
 /* Tile shape of the 3D streaming kernel (the xy block each CTA streams
  * along z; the temporal blocking of Section 3.2 recomputes a halo of k cells
- * around it).  Tiles 0..AC_NUM_TILES_3D-1 (FP32 storage; FP64 tiles are half
- * as wide in x):
- *   0: 128 x 32 outputs, 3 vectors per thread (one CTA per SM)
- *   1: 128 x 16 outputs, several CTAs per SM
- *   2: 128 x 32 outputs, 2 vectors per thread (more warps per CTA)
+ * around it).  Tiles 0..AC_NUM_TILES_3D-1 (FP32 / FP16 storage; FP64 tiles
+ * are half as wide in x):
+ *   0: 128 x 32 outputs, two rows per thread
+ *   1: 128 x 16 outputs, two rows per thread, several CTAs per SM
+ *   2: 128 x 32 outputs, four rows per thread (FP16 storage: one)
  * AC_TILE_AUTO (-1) restores the autotuned or default choice.  2D grids
  * accept tile 0 only (AC_ERR_UNSUPPORTED otherwise).  The result of a step
  * does not depend on the tile. */

@@ -240,13 +240,14 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
   default_schedule(c, variant, k);
 }
 
-// Default 3D tile per depth, measured on GB300 (512^3 FP32 / FP16, 256^3
-// FP64): k = 1 gains from several CTAs per SM (tile 1; FP64 from more warps,
-// tile 2), k = 2 from more warps per CTA (tile 2), k = 3 keeps tile 0 (the
-// others spill registers).
+// Default 3D tile per storage type and depth, measured on GB300 (512^3
+// FP32 / FP16, 256^3 FP64): two rows per thread at 128 x 32 (tile 0) for
+// k <= 2 (FP16 storage at k = 1: several CTAs per SM, tile 1); k = 3 needs
+// the register room of four rows per thread with half the threads (tile 2).
 static int default_tile(const ac_ctx *c, int k) {
-  if (c->d.dtype == AC_F64) return k == 1 ? 2 : 0;
-  return k == 1 ? 1 : k == 2 ? 2 : 0;
+  if (c->d.dtype == AC_F64) return k == 1 ? 0 : 2;
+  if (c->d.dtype == AC_F16S) return k == 1 ? 1 : 0;
+  return k == 3 ? 2 : 0;
 }
 
 // The tile of a streaming launch: the user's, else the autotuner's (when it

@@ -8,19 +8,27 @@
 //     TMA tile load of the whole halo tile (zero fill outside the domain),
 //     signalled on one mbarrier per stage;
 //   - time level l of plane Z is formed once level l-1 of plane Z+1 exists
-//     (a lag of one plane per level); each thread keeps, for its own 16-byte
-//     vectors, the last three planes of every level in a ring of registers
-//     (the z neighbours), and levels 1..k-1 also publish their newest plane
-//     in shared memory (double buffered) for the x/y neighbours of others;
+//     (a lag of one plane per level);
+//   - a thread owns R vertically adjacent 16-byte vectors (one column of R
+//     rows) and keeps, for each, the last three planes of every level in a
+//     ring of registers (the z neighbours); levels 1..k-1 also publish their
+//     newest plane in shared memory (double buffered) for the x/y
+//     neighbours of others;
 //   - x neighbours come from the adjacent lane by warp shuffle (lanes own
-//     consecutive vectors of a row), the two warp-edge lanes read them from
-//     shared memory; y neighbours are shared-memory reads;
+//     consecutive columns of a row group), the two warp-edge lanes read
+//     theirs from shared memory; y neighbours inside the thread's own rows
+//     are registers, the rows above and below its group are shared-memory
+//     reads.  All shared-memory reads of an iteration were published before
+//     its barrier, so they are issued together at its start, ahead of the
+//     wait for the new input plane;
 //   - zero-Neumann ghosts (Section 2) are clamps at the current level: a
 //     neighbour across a domain face is the boundary cell itself.  y faces
-//     are clamped shared-memory offsets; z faces copy the boundary plane into
-//     the ghost slot in the few iterations that touch them (a separate
-//     instantiation of the loop body); x faces are one select per vector
-//     when nx is a multiple of the vector width (FASTX), else per element;
+//     are clamped shared-memory offsets and, inside a row group, a select
+//     (only in tiles that hold a y face); z faces copy the boundary plane
+//     into the ghost slot in the few iterations that touch them; those
+//     iterations and y-face tiles run a separate instantiation of the loop
+//     body.  x faces are one select per vector when nx is a multiple of the
+//     vector width (FASTX), else per element;
 //   - only level k inside the tile interior and the chunk's own planes is
 //     written; the halo cells computed on the way are discarded.
 // One __syncthreads per plane; persistent CTAs loop over (tile, z-chunk)
@@ -33,19 +41,25 @@
 
 namespace ac {
 
-// Tile shapes (the autotuner picks one): TILE 0 = 32 output rows, the default
-// vectors per thread; TILE 1 = 16 output rows (several CTAs per SM, each with
-// its own barrier); TILE 2 = 32 rows with two vectors per thread (more warps).
+// Tile shapes (the autotuner picks one), out_x x out_y outputs per CTA and
+// R rows per thread: TILE 0 = 128 x 32, R = 2; TILE 1 = 128 x 16, R = 2,
+// several CTAs per SM; TILE 2 = 128 x 32, R = 4 (twice the work per thread
+// and iteration, half the threads; FP16 storage: R = 1).  FP64 tiles are
+// half as wide in x.  MINB = resident CTAs the register budget targets.  The
+// TMA box (the halo tile) is at most 256 elements in x.
 constexpr int kS3Tiles = 3;
 template <typename T, int TILE> struct S3Cfg;
 template <int TILE> struct S3Cfg<float, TILE> {
-  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 2 : 3, D = 4, KMAX = 3;
+  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
+  static constexpr int R = TILE == 2 ? 4 : 2, D = 4, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
 };
 template <int TILE> struct S3Cfg<double, TILE> {
-  static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 2 : 3, D = 4, KMAX = 2;
+  static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32;
+  static constexpr int R = TILE == 2 ? 4 : 2, D = 4, KMAX = 2, MINB = TILE == 1 ? 2 : 1;
 };
 template <int TILE> struct S3Cfg<__half, TILE> {
-  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32, VPT = TILE == 2 ? 1 : 2, D = 4, KMAX = 3;
+  static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
+  static constexpr int R = TILE == 2 ? 1 : 2, D = 4, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
 };
 
 template <typename T, int K, int TILE = 0>
@@ -53,21 +67,22 @@ struct S3Geom {
   using Cfg = S3Cfg<T, TILE>;
   using C = typename Traits<T>::C;
   static constexpr int V = Traits<T>::V;
+  // one step per pass is bound by HBM latency: a deeper TMA ring pays there
+  static constexpr int R = Cfg::R, D = K == 1 ? 6 : Cfg::D, MINB = Cfg::MINB;
   static constexpr int HX = V * ((K + V - 1) / V);
   static constexpr int OX = Cfg::OX, OY = Cfg::OY;
-  static constexpr int TX = OX + 2 * HX, TXV = TX / V, TY = OY + 2 * K;
-  static constexpr int NVEC = TXV * TY;
-  static constexpr int VPT = Cfg::VPT;
-  static constexpr int NT = ((NVEC + VPT - 1) / VPT + 31) / 32 * 32;
-  static constexpr int D = Cfg::D;
-  static constexpr int MINB = TILE == 1 ? 2 : 1;  // resident CTAs the register budget targets
+  static constexpr int TX = OX + 2 * HX, TXV = TX / V;
+  static constexpr int TY = (OY + 2 * K + R - 1) / R * R;  // rows, whole groups of R
+  static constexpr int NSLOT = TXV * (TY / R);             // (column, row group) slots
+  static constexpr int NT = (NSLOT + 31) / 32 * 32;        // one slot per thread
   static constexpr int STAGE_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
   static constexpr int LVL_BYTES = TX * TY * (int)sizeof(C);
   static constexpr int LVL_TOTAL = (K > 1 ? 2 * (K - 1) * LVL_BYTES : 0);
   static constexpr int SMEM = D * STAGE_STRIDE + LVL_TOTAL + D * 8 + 16;
   static_assert(NT <= 1024, "tile too large for one CTA");
-  static_assert(VPT * NT >= NVEC, "vector slots");
+  static_assert(SMEM <= 227 * 1024, "tile too large for shared memory");
+  static_assert(TY <= 256 && TX <= 256, "TMA box limits");
 };
 
 template <typename T, int V>
@@ -109,8 +124,8 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
                int tiles_x, int tiles_y, int nzc, int zchunk) {
   using Gm = S3Geom<T, K, TILE>;
   using C = typename Traits<T>::C;
-  constexpr int V = Gm::V, VPT = Gm::VPT, TXV = Gm::TXV, TY = Gm::TY, TX = Gm::TX, D = Gm::D;
-  constexpr int NT = Gm::NT, NVEC = Gm::NVEC;
+  constexpr int V = Gm::V, R = Gm::R, TXV = Gm::TXV, TY = Gm::TY, TX = Gm::TX, D = Gm::D;
+  constexpr int NSLOT = Gm::NSLOT;
   constexpr int PLANE = TX * TY;  // elements per plane buffer
   extern __shared__ __align__(128) unsigned char smem[];
   // stage s of the TMA ring starts at byte s * STAGE_STRIDE
@@ -128,34 +143,34 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
   }
   __syncthreads();
 
-  // this thread's vector slots: q = tid + j*NT -> tile row qr, vector column qc
-  int qr[VPT], qc[VPT];
-  bool qv[VPT];
-#pragma unroll
-  for (int j = 0; j < VPT; ++j) {
-    const int q = tid + j * NT;
-    qv[j] = q < NVEC;
-    const int qq = qv[j] ? q : NVEC - 1;
-    qr[j] = qq / TXV;
-    qc[j] = qq - qr[j] * TXV;
-  }
+  // this thread's slot: vector column qc of rows R*qg .. R*qg + R-1 (threads
+  // past the last slot duplicate it and store nothing)
+  const bool qv = tid < NSLOT;
+  const int qq = qv ? tid : NSLOT - 1;
+  const int qg = qq / TXV, qc = qq - qg * TXV;
+  const int r0 = R * qg;
   const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
   const int64_t plane_stride = g.pitch * g.ny;
   const C alpha = (C)g.alpha, beta = (C)g.beta;
+  // the two warp-edge lanes take one x neighbour from shared memory (lane 0
+  // the left one, lane 31 the right one) unless it lies outside the tile
+  const bool lsm = lane == 0 && qc > 0;
+  const bool rsm = lane == 31 && qc < TXV - 1;
+  const bool esm = lsm || rsm;
 
   // Level l keeps its last three planes in a ring of register slots: at
   // iteration t slot t%3 holds plane Z+1 (newest), (t+2)%3 plane Z and
   // (t+1)%3 plane Z-1 of the stencil that forms level l+1 of plane Z.  The
   // plane loop is unrolled by three so that every slot index is a constant.
-  C ring[K][3][VPT][V];
+  C ring[K][3][R][V];
 #pragma unroll
   for (int l = 0; l < K; ++l)
 #pragma unroll
     for (int s = 0; s < 3; ++s)
 #pragma unroll
-      for (int j = 0; j < VPT; ++j)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int e = 0; e < V; ++e) ring[l][s][j][e] = C(0);
+        for (int e = 0; e < V; ++e) ring[l][s][i][e] = C(0);
 
   uint32_t slot = 0;  // planes consumed so far by this CTA: ring position and phase
   const int items = tiles_x * tiles_y * nzc;
@@ -178,42 +193,55 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       }
     }
 
-    // Per-item facts of this thread's vectors.  y neighbours are read at
-    // shared-memory offsets clamped to the domain (row gy = 0 reads itself
-    // as its lower neighbour, gy = ny-1 as its upper one: the zero-Neumann
-    // ghost) and to the tile.
+    // Per-item facts of this slot.  Rows rlo / rhi of the tile are the
+    // domain's y = 0 / y = ny-1 rows (clamped to the tile): their outer
+    // neighbour is the row itself, the zero-Neumann ghost.
     const int rlo = max(0, -by), rhi = min(TY - 1, ny - 1 - by);
+    const bool yface = rlo > 0 || rhi < TY - 1;
     const bool xedge = (bx <= 0) || (bx + TX > nx - 1);
-    int own[VPT], ysn[VPT], ynn[VPT], lnb[VPT], rnb[VPT], gxv[VPT];
-    bool st_ok[VPT], st_full[VPT], lfix[VPT], rfix[VPT];
-    int64_t goff[VPT];
+    const int own = r0 * TX + qc * V;                 // row i at own + i * TX
+    const int ysn = max(r0 - 1, rlo) * TX + qc * V;   // row below the group
+    const int ynn = min(r0 + R, rhi) * TX + qc * V;   // row above the group
+    const int eoff = esm ? own + (lane == 0 ? -1 : V) : own;  // the edge lane's x neighbour
+    const int gx0 = bx + qc * V;
+    const bool lfix = gx0 == 0;               // element 0 is the x = 0 face
+    const bool rfix = gx0 + V - 1 == nx - 1;  // element V-1 is the x = nx-1 face
+    const bool st_full = gx0 + V <= nx;
+    const bool st_col = qv && qc >= Gm::HX / V && qc < (Gm::HX + Gm::OX) / V && gx0 < nx;
+    bool st_row[R];
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-      const int r = qr[j], c = qc[j];
-      own[j] = r * TX + c * V;
-      ysn[j] = max(r - 1, rlo) * TX + c * V;
-      ynn[j] = min(r + 1, rhi) * TX + c * V;
-      lnb[j] = (lane == 0 && c > 0) ? own[j] - 1 : -1;
-      rnb[j] = (lane == 31 && c < TXV - 1) ? own[j] + V : -1;
-      const int gy = by + r, gx = bx + c * V;
-      gxv[j] = gx;
-      lfix[j] = gx == 0;               // element 0 is the x = 0 face
-      rfix[j] = gx + V - 1 == nx - 1;  // element V-1 is the x = nx-1 face
-      st_ok[j] = qv[j] && r >= K && r < K + Gm::OY && c >= Gm::HX / V &&
-                 c < (Gm::HX + Gm::OX) / V && gy < ny && gx < nx;
-      st_full[j] = gx + V <= nx;
-      goff[j] = (int64_t)gy * g.pitch + gx;
-    }
+    for (int i = 0; i < R; ++i)
+      st_row[i] = st_col && r0 + i >= K && r0 + i < K + Gm::OY && by + r0 + i < ny;
+    const int64_t goff = (int64_t)(by + r0) * g.pitch + gx0;
 
     auto body = [&]<int P, bool BND>(int t) -> bool {
       constexpr int SN = P, SB = (P + 2) % 3, SA = (P + 1) % 3;
+      // Shared-memory reads of this iteration: level 0 reads the stage of
+      // plane t-1, level l >= 1 the level-l plane of the previous iteration.
+      C ys[K][V], yn[K][V], ev[K][R];
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        if (l == 0) {
+          const T *cb = stage_ptr((int)((slot + t + D - 1) % D));
+          ld_vec<T, V>(cb, ysn, ys[0]);
+          ld_vec<T, V>(cb, ynn, yn[0]);
+#pragma unroll
+          for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
+        } else {
+          const C *cb = lvl + ((l - 1) * 2 + ((t + 1) & 1)) * PLANE;
+          ld_vec_c<V>(cb, ysn, ys[l]);
+          ld_vec_c<V>(cb, ynn, yn[l]);
+#pragma unroll
+          for (int i = 0; i < R; ++i) ev[l][i] = esm ? cb[eoff + i * TX] : C(0);
+        }
+      }
       if (!BND || t < n_in) {
         const uint32_t u = slot + t;
         const int s = (int)(u % D);
         if (!mbar_wait_bounded(&bars[s], (u / D) & 1u)) abort_flag = 1;
         const T *stage = stage_ptr(s);
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) ld_vec<T, V>(stage, own[j], ring[0][SN][j]);
+        for (int i = 0; i < R; ++i) ld_vec<T, V>(stage, own + i * TX, ring[0][SN][i]);
       }
 #pragma unroll
       for (int l = 0; l < K; ++l) {
@@ -221,41 +249,34 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
         if constexpr (BND) {
           if (Z == 0) {                   // ghost below the bottom face
 #pragma unroll
-            for (int j = 0; j < VPT; ++j)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-              for (int e = 0; e < V; ++e) ring[l][SA][j][e] = ring[l][SB][j][e];
+              for (int e = 0; e < V; ++e) ring[l][SA][i][e] = ring[l][SB][i][e];
           }
           if (Z == nz - 1) {              // ghost above the top face
 #pragma unroll
-            for (int j = 0; j < VPT; ++j)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-              for (int e = 0; e < V; ++e) ring[l][SN][j][e] = ring[l][SB][j][e];
+              for (int e = 0; e < V; ++e) ring[l][SN][i][e] = ring[l][SB][i][e];
           }
         }
         const int ZK = lo0 + t - K;
         const bool store = (l == K - 1) && ZK >= z0 && ZK < z1;
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-          const C *mid = ring[l][SB][j];
-          C sv[V], nv[V], wl, er;
+        for (int i = 0; i < R; ++i) {
+          const C *mid = ring[l][SB][i];
+          const C *sp = i == 0 ? ys[l] : ring[l][SB][i - 1];
+          const C *np = i == R - 1 ? yn[l] : ring[l][SB][i + 1];
+          // inside the group a domain y face is a select (y-face tiles only)
+          const bool sself = BND && i > 0 && r0 + i == rlo;
+          const bool nself = BND && i < R - 1 && r0 + i == rhi;
           const C sh_l = __shfl_up_sync(0xffffffffu, mid[V - 1], 1);
           const C sh_r = __shfl_down_sync(0xffffffffu, mid[0], 1);
-          if (l == 0) {
-            const T *cb = stage_ptr((int)((slot + t + D - 1) % D));
-            ld_vec<T, V>(cb, ysn[j], sv);
-            ld_vec<T, V>(cb, ynn[j], nv);
-            wl = lnb[j] >= 0 ? to_c(cb[lnb[j]]) : sh_l;
-            er = rnb[j] >= 0 ? to_c(cb[rnb[j]]) : sh_r;
-          } else {
-            const C *cb = lvl + ((l - 1) * 2 + ((t + 1) & 1)) * PLANE;
-            ld_vec_c<V>(cb, ysn[j], sv);
-            ld_vec_c<V>(cb, ynn[j], nv);
-            wl = lnb[j] >= 0 ? cb[lnb[j]] : sh_l;
-            er = rnb[j] >= 0 ? cb[rnb[j]] : sh_r;
-          }
+          C wl = lsm ? ev[l][i] : sh_l;
+          C er = rsm ? ev[l][i] : sh_r;
           if constexpr (FASTX) {
-            wl = lfix[j] ? mid[0] : wl;
-            er = rfix[j] ? mid[V - 1] : er;
+            wl = lfix ? mid[0] : wl;
+            er = rfix ? mid[V - 1] : er;
           }
           C out[V];
 #pragma unroll
@@ -265,26 +286,31 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
             C ea = (e == V - 1) ? er : mid[e + 1];
             if constexpr (!FASTX) {
               if (xedge) {
-                const int gx = gxv[j] + e;
+                const int gx = gx0 + e;
                 if (gx == 0) w = p;
                 if (gx == nx - 1) ea = p;
               }
             }
-            const C nsum = ((w + ea) + (sv[e] + nv[e])) + (ring[l][SA][j][e] + ring[l][SN][j][e]);
+            C sv = sp[e], nv = np[e];
+            if constexpr (BND) {
+              sv = sself ? p : sv;
+              nv = nself ? p : nv;
+            }
+            const C nsum = ((w + ea) + (sv + nv)) + (ring[l][SA][i][e] + ring[l][SN][i][e]);
             out[e] = ac_update<C>(p, nsum, C(-6), alpha, beta);
           }
           if (l + 1 < K) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) ring[l + 1 < K ? l + 1 : 0][SN][j][e] = out[e];
-            if (qv[j]) st_vec_c<V>(lvl + (l * 2 + (t & 1)) * PLANE, own[j], out);
-          } else if (store && st_ok[j]) {
-            T *d = dst + (int64_t)ZK * plane_stride + goff[j];
-            if (st_full[j]) {
+            for (int e = 0; e < V; ++e) ring[l + 1 < K ? l + 1 : 0][SN][i][e] = out[e];
+            if (qv) st_vec_c<V>(lvl + (l * 2 + (t & 1)) * PLANE, own + i * TX, out);
+          } else if (store && st_row[i]) {
+            T *d = dst + (int64_t)ZK * plane_stride + goff + (int64_t)i * g.pitch;
+            if (st_full) {
               *reinterpret_cast<uint4 *>(d) = pack16<T>(out);
             } else {
 #pragma unroll
               for (int e = 0; e < V; ++e)
-                if (gxv[j] + e < nx) d[e] = from_c<T>(out[e]);
+                if (gx0 + e < nx) d[e] = from_c<T>(out[e]);
             }
           }
         }
@@ -314,12 +340,13 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
 
     // Iterations that touch a z face (ghost copies) or run past the last
     // input plane take the BND body: t in [1, K] when the chunk starts at
-    // z = 0, and t >= nz - lo0 when it ends at the top face.
+    // z = 0, and t >= nz - lo0 when it ends at the top face; so does every
+    // iteration of a tile that holds a y face.
     const int bnd_lo_end = (lo0 == 0) ? K : -1;
     const int bnd_hi_begin = (hi0 == nz) ? nz - lo0 - 1 : n_iter;
     int t = 0;
     for (; t + 3 <= n_iter; t += 3) {
-      const bool bnd = (t <= bnd_lo_end) || (t + 2 >= bnd_hi_begin);
+      const bool bnd = yface || (t <= bnd_lo_end) || (t + 2 >= bnd_hi_begin);
       if (bnd) {
         if (!body.template operator()<0, true>(t)) return;
         if (!body.template operator()<1, true>(t + 1)) return;

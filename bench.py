@@ -424,6 +424,8 @@ def run_ours(args, ws, rank, local):
     if args.k:
         sim.set_schedule(ac.AC_VARIANT_STREAM if args.k > 0 else ac.AC_VARIANT_DIRECT, abs(args.k))
     variant, k = sim.schedule()
+    tile = sim.tile()
+    kid = f"{kname} k={k}" + (f" tile={tile}" if len(w.shape) == 3 else "")
     es = {"f64": 8, "f32": 4, "f16s": 2}[dtype]
     field_bytes = w.cells * es
 
@@ -472,7 +474,7 @@ def run_ours(args, ws, rank, local):
     alg_bytes = 2 * field_bytes
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic = recorded_traffic(f"{kname} k={k}", ksrc) if variant == ac.AC_VARIANT_STREAM else None
+    traffic = recorded_traffic(kid, ksrc) if variant == ac.AC_VARIANT_STREAM else None
 
     # end to end through the public API with host buffers: H2D of the initial
     # state from pinned memory, the steps, D2H of the final field + the energy
@@ -506,12 +508,13 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.shape), "euler_steps_per_job": w.steps,
                    "eps": w.eps, "h": w.h, "dt": w.dt, "init": w.init,
-                   "schedule": {"variant": "stream" if variant == 2 else "direct", "k": k},
+                   "schedule": {"variant": "stream" if variant == 2 else "direct", "k": k,
+                                "tile": tile},
                    "parallelism": f"replicas x{ws}",
                    "l2": "no flush: two field buffers of %d MiB each exceed L2" % (field_bytes >> 20)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"{kname} k={k}", "peak_kind": peak_kind,
+                     "kernel": kid, "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                      "effective_frac_k1": value / ws * 2 * es / peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,

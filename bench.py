@@ -170,18 +170,26 @@ def init_field(sim, w):
 
 
 # ------------------------------------------------------------ CPU oracle ---
-def oracle_sample(w, target_s: float, max_steps: int = 400):
-    """Time the FP64 oracle on the same grid for a bounded number of steps."""
+def oracle_sample(w, target_s: float, max_steps: int = 2000):
+    """Time the FP64 oracle on the same grid for a bounded number of steps
+    (sized from a 1-step and a 5-step calibration so that the timed sample
+    takes about target_s; the per-call cost of allocating the output field
+    is separated from the per-step cost)."""
     import numpy as np
     import oracle
     if w.init == "sphere":
         phi0 = oracle.init_sphere(w.shape, w.h, w.r0, w.eps).astype(np.float32).astype(np.float64)
     else:
         phi0 = oracle.init_random(w.shape, seed=w.seed).astype(np.float32).astype(np.float64)
+    phi = oracle.step(phi0, w.h, w.eps, w.dt, 1)  # warm-up: threads, first touch
     t0 = time.perf_counter()
-    phi = oracle.step(phi0, w.h, w.eps, w.dt, 1)
+    phi = oracle.step(phi, w.h, w.eps, w.dt, 1)
     t1 = time.perf_counter() - t0
-    steps = int(max(1, min(max_steps, target_s / max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    phi = oracle.step(phi, w.h, w.eps, w.dt, 5)
+    t5 = time.perf_counter() - t0
+    per_step = max((t5 - t1) / 4.0, t5 / 20.0, 1e-9)
+    steps = int(max(1, min(max_steps, target_s / per_step)))
     t0 = time.perf_counter()
     oracle.step(phi, w.h, w.eps, w.dt, steps)
     dt_s = time.perf_counter() - t0
@@ -530,6 +538,15 @@ def run_ours(args, ws, rank, local):
             "value": w.cells * steps / secs / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{w.name}: all {w.cells} cells, {steps} Euler steps of the FP64 oracle "
                       f"(the job runs {w.steps}); {secs:.1f} s"}
+        import oracle
+        oracle.set_num_threads(1)
+        try:
+            steps1, secs1, _ = oracle_sample(w, args.cpu_seconds / 4)
+        finally:
+            oracle.set_num_threads(0)
+        out["cpu_baseline"]["single_core"] = {
+            "value": w.cells * steps1 / secs1 / 1e9, "unit": UNIT,
+            "sample": f"{steps1} Euler steps on one thread; {secs1:.1f} s"}
     sim.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

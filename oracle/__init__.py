@@ -41,6 +41,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_energy.restype = dbl
         L.oracle_phase_volume.argtypes = [i64, i64, i64, dbl, dp]
         L.oracle_phase_volume.restype = dbl
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_num_threads.restype = None
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
@@ -145,3 +147,8 @@ def eps_m(h: float, m: float) -> float:
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops; n <= 0 restores all cores."""
+    lib().oracle_set_num_threads(int(n))

@@ -265,6 +265,15 @@ EXPORT double oracle_phase_volume(int64_t nx, int64_t ny, int64_t nz, double h,
   return hd * s;
 }
 
+/* Threads of the following OpenMP loops (n <= 0 restores the default). */
+EXPORT void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the stepping loops use (1 without OpenMP). */
 EXPORT int oracle_num_threads(void) {
 #ifdef _OPENMP

@@ -134,6 +134,28 @@ int ac_init_sphere(ac_ctx *ctx, double lower_x, double lower_y, double lower_z,
                    double cx, double cy, double cz, double r0);
 int ac_init_random(ac_ctx *ctx, uint64_t seed, double amplitude);
 
+/* The further initial shapes of Section 3.1 (Eqs. 2Ddumbellini,
+ * 3Ddumbellini, 2Dstarini, 3Dstarini, 2Dtorusini, 3Dtorusini), generated on
+ * the device at the cell centres lower + (i + 0.5) h, in FP64 with
+ * w = sqrt(2) eps, rounded once to the storage type:
+ *   AC_SHAPE_DUMBBELL (p0 = R0; domain (0,2) x (0,1) [x (0,1)]): 1 inside the
+ *     bar 0.4 < x < 1.6, 0.4 < y [, z] < 0.6, else 1 + tanh((R0 - d_l)/w)
+ *     + tanh((R0 - d_r)/w), d_l, d_r the distances to (0.3, 0.5 [, 0.5]) and
+ *     (1.7, 0.5 [, 0.5]);
+ *   AC_SHAPE_STAR (no parameters): 2D tanh((0.25 + 0.1 cos 6t - r)/w) about
+ *     (0.5, 0.5) (unit square); 3D tanh((0.7 + 0.2 cos 6t - |p|)/w) on
+ *     (-1,1)^3 with t the polar angle of (x, z) about the origin (the
+ *     printed test "x > 0.5" read as the 2D form's);
+ *   AC_SHAPE_TORUS (p0 = R1, p1 = R2): 2D annulus -1 + tanh((R1 - r)/w)
+ *     - tanh((R2 - r)/w) about (0.5, 0.5); 3D the printed signed distance
+ *     d = sqrt(z^2 + (sqrt(x^2 + y^2) - R1)^2) - R2 to a ring about the z
+ *     axis, used as tanh(-d/w) (phase +1 inside the tube).
+ * Unused parameters are ignored.  AC_ERR_INVALID for an unknown kind or a
+ * non-finite value.  Asynchronous on the context's stream. */
+enum { AC_SHAPE_DUMBBELL = 1, AC_SHAPE_STAR = 2, AC_SHAPE_TORUS = 3 };
+int ac_init_shape(ac_ctx *ctx, int32_t kind, double lower_x, double lower_y, double lower_z,
+                  double p0, double p1);
+
 /* ------------------------------------------------------- scheduling ---- */
 /* Kernel variants selectable with ac_set_schedule. */
 enum {

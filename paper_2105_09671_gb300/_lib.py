@@ -24,10 +24,11 @@ AC_F64, AC_F32, AC_F16S = 0, 1, 2
 AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM = 0, 1, 2
 AC_MAX_K = 8
 AC_TILE_AUTO, AC_NUM_TILES_3D = -1, 3
+AC_SHAPE_DUMBBELL, AC_SHAPE_STAR, AC_SHAPE_TORUS = 1, 2, 3
 
 EXPORTED = (
     "ac_workspace_bytes", "ac_create", "ac_step", "ac_energy", "ac_phase_volume", "ac_observe",
-    "ac_init_sphere", "ac_init_random", "ac_set_schedule", "ac_get_schedule", "ac_set_tile",
+    "ac_init_sphere", "ac_init_random", "ac_init_shape", "ac_set_schedule", "ac_get_schedule", "ac_set_tile",
     "ac_get_tile", "ac_autotune",
     "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
     "ac_last_error", "ac_version",
@@ -119,6 +120,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_observe": [vp, ctypes.POINTER(dbl)],
         "ac_init_sphere": [vp, dbl, dbl, dbl, dbl, dbl, dbl, dbl],
         "ac_init_random": [vp, u64, dbl],
+        "ac_init_shape": [vp, i32, dbl, dbl, dbl, dbl, dbl],
         "ac_set_schedule": [vp, i32, i32],
         "ac_get_schedule": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "ac_set_tile": [vp, i32],
@@ -229,6 +231,12 @@ def ac_init_sphere(ctx: int, lower=(0.0, 0.0, 0.0), center=(0.5, 0.5, 0.5), r0: 
 
 def ac_init_random(ctx: int, seed: int, amplitude: float = 0.1) -> None:
     check(lib().ac_init_random(ctypes.c_void_p(ctx), int(seed), float(amplitude)))
+
+
+def ac_init_shape(ctx: int, kind: int, lower=(0.0, 0.0, 0.0), p0: float = 0.0,
+                  p1: float = 0.0) -> None:
+    check(lib().ac_init_shape(ctypes.c_void_p(ctx), int(kind), float(lower[0]), float(lower[1]),
+                              float(lower[2]), float(p0), float(p1)))
 
 
 def ac_set_schedule(ctx: int, variant: int, k: int) -> None:

@@ -461,6 +461,22 @@ extern "C" int ac_init_sphere(ac_ctx *c, double lx, double ly, double lz, double
   return AC_OK;
 }
 
+extern "C" int ac_init_shape(ac_ctx *c, int32_t kind, double lx, double ly, double lz, double p0,
+                             double p1) {
+  if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
+  if (kind != AC_SHAPE_DUMBBELL && kind != AC_SHAPE_STAR && kind != AC_SHAPE_TORUS)
+    return fail(AC_ERR_INVALID, "unknown shape %d", kind);
+  if (!std::isfinite(lx) || !std::isfinite(ly) || !std::isfinite(lz) || !std::isfinite(p0) ||
+      !std::isfinite(p1))
+    return fail(AC_ERR_INVALID, "shape parameters must be finite");
+  const double lo[3] = {lx, ly, lz};
+  cudaError_t e = launch_init_shape(c->d.dtype, c->gp, c->phi, kind, c->d.ndim, c->d.h, lo, p0, p1,
+                                    c->d.eps, c->stream);
+  if (e != cudaSuccess) return fail(AC_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
+  ++c->launches;
+  return AC_OK;
+}
+
 extern "C" int ac_init_random(ac_ctx *c, uint64_t seed, double amplitude) {
   if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
   if (!std::isfinite(amplitude)) return fail(AC_ERR_INVALID, "amplitude must be finite");

@@ -3,6 +3,7 @@
 //   sphere/circle: phi = tanh((r0 - |x - c|) / (sqrt(2) eps)) at the cell
 //                  centres x_i = lower + (i + 1/2) h (Section 2), in FP64,
 //                  rounded once (nearest-even) to the storage type.
+//   dumbbell, star, torus: the further shapes of Section 3.1 (shape_value);
 //   random:        phi = amplitude * (2 u - 1), u = (z >> 11) * 2^-53, with z
 //                  the SplitMix64 output number (c + 1) for seed s and cell
 //                  linear index c (Steele, Lea, Flood, OOPSLA 2014).
@@ -51,6 +52,99 @@ __global__ void init_random_k(T *__restrict__ phi, GridParams g, uint64_t seed, 
   const double r = __dsub_rn(__dmul_rn(2.0, u), 1.0);
   const double v = __dmul_rn(amp, r);
   phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
+}
+
+// Polar angle of the star (Section 3.1): atan(v/u) for u > 0, pi + atan(v/u)
+// otherwise; u == 0 takes the limits +-pi/2 of atan (0 at the centre).
+__device__ __forceinline__ double star_theta(double u, double v) {
+  double base;
+  if (u == 0.0)
+    base = v > 0.0 ? 1.5707963267948966 : (v < 0.0 ? -1.5707963267948966 : 0.0);
+  else
+    base = atan(__ddiv_rn(v, u));
+  return u > 0.0 ? base : __dadd_rn(3.141592653589793, base);
+}
+
+// The further shapes of Section 3.1 at one point (FP64, every operation
+// rounded separately as written):
+//   dumbbell: 1 inside the bar 0.4 < x < 1.6, 0.4 < y (, z) < 0.6, else
+//             1 + tanh((p0 - |p - (0.3, .5[, .5])|)/w) + tanh((p0 - |p - (1.7, .5[, .5])|)/w)
+//   star:     2D tanh((0.25 + 0.1 cos 6t - |p - (.5, .5)|)/w), t the angle about (.5, .5);
+//             3D tanh((0.7 + 0.2 cos 6t - |p|)/w), t the angle of (x, z) about 0
+//   torus:    2D -1 + tanh((p0 - r)/w) - tanh((p1 - r)/w), r = |p - (.5, .5)|;
+//             3D tanh((p1 - sqrt(z^2 + (sqrt(x^2 + y^2) - p0)^2))/w)
+// with w = sqrt(2) eps.
+__device__ double shape_value(int kind, int ndim, double x, double y, double z, double p0,
+                              double p1, double w) {
+  if (kind == AC_SHAPE_DUMBBELL) {
+    double tr = __dmul_rn(__dsub_rn(y, 0.5), __dsub_rn(y, 0.5));
+    bool bar = x > 0.4 && x < 1.6 && y > 0.4 && y < 0.6;
+    if (ndim == 3) {
+      tr = __dadd_rn(tr, __dmul_rn(__dsub_rn(z, 0.5), __dsub_rn(z, 0.5)));
+      bar = bar && z > 0.4 && z < 0.6;
+    }
+    if (bar) return 1.0;
+    const double dl = __dsub_rn(x, 0.3), dr = __dsub_rn(x, 1.7);
+    const double left = tanh(__ddiv_rn(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dl, dl), tr))), w));
+    const double right = tanh(__ddiv_rn(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dr, dr), tr))), w));
+    return __dadd_rn(__dadd_rn(1.0, left), right);
+  }
+  if (kind == AC_SHAPE_STAR) {
+    if (ndim == 2) {
+      const double u = __dsub_rn(x, 0.5), v = __dsub_rn(y, 0.5);
+      const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
+      const double rs = __dadd_rn(0.25, __dmul_rn(0.1, cos(__dmul_rn(6.0, star_theta(u, v)))));
+      return tanh(__ddiv_rn(__dsub_rn(rs, r), w));
+    }
+    const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    const double rs = __dadd_rn(0.7, __dmul_rn(0.2, cos(__dmul_rn(6.0, star_theta(x, z)))));
+    return tanh(__ddiv_rn(__dsub_rn(rs, r), w));
+  }
+  // torus
+  if (ndim == 2) {
+    const double u = __dsub_rn(x, 0.5), v = __dsub_rn(y, 0.5);
+    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
+    return __dsub_rn(__dadd_rn(-1.0, tanh(__ddiv_rn(__dsub_rn(p0, r), w))),
+                     tanh(__ddiv_rn(__dsub_rn(p1, r), w)));
+  }
+  const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  const double q = __dsub_rn(rho, p0);
+  const double d = __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(z, z), __dmul_rn(q, q))), p1);
+  return tanh(__ddiv_rn(-d, w));
+}
+
+template <typename T>
+__global__ void init_shape_k(T *__restrict__ phi, GridParams g, int kind, int ndim, double h,
+                             double lx, double ly, double lz, double p0, double p1, double width) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  const int64_t k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const double x = __dadd_rn(lx, __dmul_rn(__dadd_rn((double)i, 0.5), h));
+  const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));
+  const double z = __dadd_rn(lz, __dmul_rn(__dadd_rn((double)k, 0.5), h));
+  phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(shape_value(kind, ndim, x, y, z, p0, p1, width));
+}
+
+template <typename T>
+static cudaError_t shape_t(const GridParams &g, void *phi, int kind, int ndim, double h,
+                           const double *lo, double p0, double p1, double eps, cudaStream_t s) {
+  dim3 block(64, 4);
+  dim3 grid((unsigned)((g.nx + 63) / 64), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz);
+  init_shape_k<T><<<grid, block, 0, s>>>((T *)phi, g, kind, ndim, h, lo[0], lo[1], lo[2], p0, p1,
+                                         sqrt(2.0) * eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_shape(int dtype, const GridParams &g, void *phi, int kind, int ndim,
+                              double h, const double lower[3], double p0, double p1, double eps,
+                              cudaStream_t s) {
+  switch (dtype) {
+    case AC_F64: return shape_t<double>(g, phi, kind, ndim, h, lower, p0, p1, eps, s);
+    case AC_F32: return shape_t<float>(g, phi, kind, ndim, h, lower, p0, p1, eps, s);
+    case AC_F16S: return shape_t<__half>(g, phi, kind, ndim, h, lower, p0, p1, eps, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>

@@ -57,6 +57,9 @@ cudaError_t launch_guard(const float *phi, const float *phat, const GridParams &
 cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double h,
                                const double lower[3], const double center[3], double r0,
                                double eps, cudaStream_t s);
+cudaError_t launch_init_shape(int dtype, const GridParams &g, void *phi, int kind, int ndim,
+                              double h, const double lower[3], double p0, double p1, double eps,
+                              cudaStream_t s);
 cudaError_t launch_init_random(int dtype, const GridParams &g, void *phi, uint64_t seed,
                                double amplitude, cudaStream_t s);
 

@@ -105,6 +105,18 @@ class Simulation:
     def init_random(self, seed: int, amplitude: float = 0.1) -> None:
         L.ac_init_random(self.ctx, seed, amplitude)
 
+    def init_shape(self, kind: str, lower=(0.0, 0.0, 0.0), **params) -> None:
+        """Dumbbell (r0), star, or torus (r1, r2) of Section 3.1 on the device."""
+        if kind == "dumbbell":
+            L.ac_init_shape(self.ctx, L.AC_SHAPE_DUMBBELL, lower, params.get("r0", 0.2))
+        elif kind == "star":
+            L.ac_init_shape(self.ctx, L.AC_SHAPE_STAR, lower)
+        elif kind == "torus":
+            L.ac_init_shape(self.ctx, L.AC_SHAPE_TORUS, lower, params.get("r1", 0.4),
+                            params.get("r2", 0.3))
+        else:
+            raise ValueError(f"unknown shape {kind!r}")
+
     def set_schedule(self, variant: int, k: int) -> None:
         L.ac_set_schedule(self.ctx, variant, k)
 

@@ -97,3 +97,53 @@ def batch_instances(count: int = 512, seed: int = 0, steps: int = 2000):
         out.append(dict(n=n, h=h, eps=eps, dt=0.1 * h * h, init="sphere" if i % 2 == 0 else "random",
                         r0=r0, seed=1000 + i, steps=steps))
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class ShapeCase:
+    """One of the paper's mean-curvature / separation runs (Section 3.2, 3.3,
+    Tables 1-3), with the interface width eps_m given by its m (Eq. emvalue).
+
+    Readings: h is the domain length over the cell count (on (0, 2) x (0, 1)
+    the dumbbell's 400 x 200 cells have h = 1/200; on (-1, 1)^3, 200 cells
+    per side give h = 0.01); the step count is the printed final time T over
+    dt = 0.1 h^2 (where a table's iteration count disagrees with T, T wins)."""
+    name: str
+    kind: str             # "dumbbell", "star", "torus", "sphere" or "random"
+    shape: tuple          # (ny, nx) or (nz, ny, nx)
+    h: float
+    m: float              # eps = eps_m(h, m)
+    steps: int
+    lower: tuple = (0.0, 0.0, 0.0)
+    params: tuple = ()    # dumbbell (r0,), torus (r1, r2), sphere (r0,)
+    seed: int = 0
+
+    @property
+    def ndim(self) -> int:
+        return len(self.shape)
+
+    @property
+    def dt(self) -> float:
+        return 0.1 * self.h * self.h
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.shape))
+
+
+# Table 3's runs: 2D with eps_10 on 200^2 (dumbbell 400 x 200 on (0,2)x(0,1));
+# 3D with eps_12 on 100^3 (dumbbell 200 x 100 x 100; star and torus on
+# (-1,1)^3 with 200 cells per side).
+PAPER_CASES = (
+    ShapeCase("circle2d", "sphere", (200, 200), 1 / 200, 10, 12000, params=(0.25,)),
+    ShapeCase("dumbbell2d", "dumbbell", (200, 400), 1 / 200, 10, 3760, params=(0.2,)),
+    ShapeCase("star2d", "star", (200, 200), 1 / 200, 10, 13000),
+    ShapeCase("torus2d", "torus", (200, 200), 1 / 200, 10, 23000, params=(0.4, 0.3)),
+    ShapeCase("separation2d", "random", (200, 200), 1 / 200, 10, 12000, seed=1),
+    ShapeCase("sphere3d", "sphere", (100, 100, 100), 1 / 100, 12, 2000, params=(0.25,)),
+    ShapeCase("dumbbell3d", "dumbbell", (100, 100, 200), 1 / 100, 12, 250, params=(0.25,)),
+    ShapeCase("star3d", "star", (200, 200, 200), 0.01, 12, 2000, lower=(-1.0, -1.0, -1.0)),
+    ShapeCase("torus3d", "torus", (200, 200, 200), 0.01, 12, 1000, lower=(-1.0, -1.0, -1.0),
+              params=(0.3, 0.3)),
+    ShapeCase("separation3d", "random", (100, 100, 100), 1 / 100, 12, 2000, seed=2),
+)

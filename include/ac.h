@@ -68,6 +68,11 @@ typedef enum {
  *   h        cell size (the paper uses h = 1/Nx).
  *   eps      interface-thickness parameter epsilon > 0 (Eq. emvalue gives
  *            the paper's choice eps_m = h m / (2 sqrt(2) atanh(0.9))).
+ *            eps = +INFINITY drops the reaction term (alpha = 0): the same
+ *            kernels then advance the heat equation phi_t = Lap phi with
+ *            explicit Euler, the kind of other explicit finite-difference
+ *            PDE the paper's conclusion names for its scheme (the energy
+ *            reduces to the Dirichlet term).
  *   dt       time step > 0.  The paper uses dt = 0.1 h^2.  The library
  *            requires dt <= h^2 / (2 ndim) (stability of the explicit
  *            Laplacian) and dt <= eps^2 (reaction step alpha = dt/eps^2

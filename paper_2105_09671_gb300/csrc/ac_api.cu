@@ -80,9 +80,10 @@ int ac_validate_desc(const ac_grid_desc *d) {
   if (d->pitch_x < d->nx) return fail(AC_ERR_INVALID, "pitch_x < nx");
   if ((d->pitch_x * (int64_t)ac_elem_size(d->dtype)) % 16 != 0)
     return fail(AC_ERR_INVALID, "pitch_x * element size must be a multiple of 16 bytes");
-  if (!(std::isfinite(d->h) && d->h > 0) || !(std::isfinite(d->eps) && d->eps > 0) ||
+  // eps = +inf is the heat equation (alpha = 0); NaN and eps <= 0 are not
+  if (!(std::isfinite(d->h) && d->h > 0) || !(d->eps > 0) ||
       !(std::isfinite(d->dt) && d->dt > 0))
-    return fail(AC_ERR_INVALID, "h, eps and dt must be finite and > 0");
+    return fail(AC_ERR_INVALID, "h and dt must be finite and > 0, eps > 0 (or +inf)");
   const double lap_limit = d->h * d->h / (2.0 * d->ndim);
   if (d->dt > lap_limit * (1.0 + 1e-12))
     return fail(AC_ERR_INVALID, "dt = %g exceeds the explicit stability limit h^2/(2 ndim) = %g",

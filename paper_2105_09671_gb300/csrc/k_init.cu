@@ -18,6 +18,15 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counte
   return z ^ (z >> 31);
 }
 
+// tanh(num / w), w > 0, with the saturated range short-cut: for
+// |num / w| >= 20 (less one rounding), 1 - tanh|a| = 2 / (e^{2|a|} + 1)
+// < 2 e^{-39.9} < 2^-54 (half an ulp below 1), so the correctly rounded value
+// is exactly +-1.  Most cells of a tanh profile lie there and skip the FP64
+// division and tanh.
+__device__ __forceinline__ double tanh_ratio(double num, double w) {
+  return fabs(num) >= __dmul_rn(20.0, w) ? copysign(1.0, num) : tanh(__ddiv_rn(num, w));
+}
+
 template <typename T>
 __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, double lx, double ly,
                               double lz, double cx, double cy, double cz, double r0,
@@ -36,7 +45,7 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
     const double dz = __dsub_rn(z, cz);
     r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
   }
-  const double v = tanh(__ddiv_rn(__dsub_rn(r0, __dsqrt_rn(r2)), width));
+  const double v = tanh_ratio(__dsub_rn(r0, __dsqrt_rn(r2)), width);
   phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
 }
 
@@ -85,8 +94,8 @@ __device__ double shape_value(int kind, int ndim, double x, double y, double z, 
     }
     if (bar) return 1.0;
     const double dl = __dsub_rn(x, 0.3), dr = __dsub_rn(x, 1.7);
-    const double left = tanh(__ddiv_rn(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dl, dl), tr))), w));
-    const double right = tanh(__ddiv_rn(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dr, dr), tr))), w));
+    const double left = tanh_ratio(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dl, dl), tr))), w);
+    const double right = tanh_ratio(__dsub_rn(p0, __dsqrt_rn(__dadd_rn(__dmul_rn(dr, dr), tr))), w);
     return __dadd_rn(__dadd_rn(1.0, left), right);
   }
   if (kind == AC_SHAPE_STAR) {
@@ -94,23 +103,23 @@ __device__ double shape_value(int kind, int ndim, double x, double y, double z, 
       const double u = __dsub_rn(x, 0.5), v = __dsub_rn(y, 0.5);
       const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
       const double rs = __dadd_rn(0.25, __dmul_rn(0.1, cos(__dmul_rn(6.0, star_theta(u, v)))));
-      return tanh(__ddiv_rn(__dsub_rn(rs, r), w));
+      return tanh_ratio(__dsub_rn(rs, r), w);
     }
     const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
     const double rs = __dadd_rn(0.7, __dmul_rn(0.2, cos(__dmul_rn(6.0, star_theta(x, z)))));
-    return tanh(__ddiv_rn(__dsub_rn(rs, r), w));
+    return tanh_ratio(__dsub_rn(rs, r), w);
   }
   // torus
   if (ndim == 2) {
     const double u = __dsub_rn(x, 0.5), v = __dsub_rn(y, 0.5);
     const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
-    return __dsub_rn(__dadd_rn(-1.0, tanh(__ddiv_rn(__dsub_rn(p0, r), w))),
-                     tanh(__ddiv_rn(__dsub_rn(p1, r), w)));
+    return __dsub_rn(__dadd_rn(-1.0, tanh_ratio(__dsub_rn(p0, r), w)),
+                     tanh_ratio(__dsub_rn(p1, r), w));
   }
   const double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
   const double q = __dsub_rn(rho, p0);
   const double d = __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(z, z), __dmul_rn(q, q))), p1);
-  return tanh(__ddiv_rn(-d, w));
+  return tanh_ratio(-d, w);
 }
 
 template <typename T>

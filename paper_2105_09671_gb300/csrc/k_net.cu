@@ -9,10 +9,11 @@
 // reads an in-bounds, unclamped shifted row.
 //
 //   net_first_fwd     1 -> 32 channels, CUDA cores (K = 9 / 27 is too short)
-//   net_conv_tc       out[p][n] = sum_t sum_c in[p+t][c] Wx[n][t][c] on the
-//                     tensor cores (tcgen05, accumulator in TMEM); forward
-//                     (bias, GELU, ghost writes) and the data gradient
-//                     (flipped taps, transposed weights, raw FP32 out)
+//   net_conv_rows     out[p][n] = sum_t sum_c in[p+t][c] Wx[n][t][c] on the
+//                     tensor cores (k_net_conv.cu: TMA row ring, tcgen05,
+//                     accumulators in TMEM); forward (bias, GELU, ghost
+//                     writes) and the data gradient (flipped taps,
+//                     transposed weights, raw FP32 out)
 //   net_dgrad_finish  adds the gradient of ghost cells to the boundary cell
 //                     they copy (adjoint of replicate padding), x gelu'
 //   net_wgrad_tc      dW[t][ci][co] = sum_p a[p+t][ci] g[p][co] on the
@@ -29,23 +30,6 @@
 
 namespace ac {
 
-__device__ __forceinline__ uint4 pack8_bf16(const float *v) {
-  uint4 u;
-  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-  return u;
-}
-__device__ __forceinline__ void unpack8_bf16(const uint4 &u, float *v) {
-  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float2 f = __bfloat1622float2(h[i]);
-    v[2 * i] = f.x;
-    v[2 * i + 1] = f.y;
-  }
-}
-
 template <int NDIM>
 __device__ __forceinline__ void decode_cell(const NetShape &sh, int64_t i, int &b, int &z, int &y,
                                             int &x) {
@@ -55,39 +39,6 @@ __device__ __forceinline__ void decode_cell(const NetShape &sh, int64_t i, int &
   i /= sh.ny;
   z = (int)(i % sh.nz);
   b = (int)(i / sh.nz);
-}
-
-// Store 32 values (one cell) at every padded position that holds this cell:
-// its interior slot and, on a domain face, the ghost slots that replicate it
-// (per axis: x+1, plus 0 if x == 0, plus n+1 if x == n-1).
-template <int NDIM>
-__device__ __forceinline__ void store_replicated(bf16 *outpad, const NetShape &sh, int b, int z,
-                                                 int y, int x, const float *a) {
-  uint4 w[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) w[c] = pack8_bf16(a + 8 * c);
-  int xs[3], ys[3], zs[3];
-  int nxs = 0, nys = 0, nzs = 0;
-  xs[nxs++] = x + 1;
-  if (x == 0) xs[nxs++] = 0;
-  if (x == sh.nx - 1) xs[nxs++] = sh.nx + 1;
-  ys[nys++] = y + 1;
-  if (y == 0) ys[nys++] = 0;
-  if (y == sh.ny - 1) ys[nys++] = sh.ny + 1;
-  if (NDIM == 3) {
-    zs[nzs++] = z + 1;
-    if (z == 0) zs[nzs++] = 0;
-    if (z == sh.nz - 1) zs[nzs++] = sh.nz + 1;
-  } else {
-    zs[nzs++] = 0;
-  }
-  for (int iz = 0; iz < nzs; ++iz)
-    for (int iy = 0; iy < nys; ++iy)
-      for (int ix = 0; ix < nxs; ++ix) {
-        uint4 *dst = reinterpret_cast<uint4 *>(outpad + sh.p(b, zs[iz], ys[iy], xs[ix]) * kNetC);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) dst[c] = w[c];
-      }
 }
 
 // ------------------------------------------------------------ first layer --
@@ -124,120 +75,11 @@ __global__ void __launch_bounds__(256) net_first_fwd_k(const float *__restrict__
       for (int c = 0; c < 4; ++c) dz[c] = pack8_bf16(acc + 8 * c);
     }
 #pragma unroll
-    for (int c = 0; c < kNetC; ++c) acc[c] = net_gelu(acc[c]);
+    for (int c = 0; c < kNetC; ++c) acc[c] = net_gelu_fast(acc[c]);
     store_replicated<NDIM>(a1pad, sh, b, z, y, x, acc);
   }
 }
 
-// ------------------------------------------------- tensor-core convolution --
-// out[p][n] = sum_{t < T} sum_{c < 32} in[p + t][c] * Wx[n][t*32 + c]
-// Tiles are 128 consecutive x positions of one row; T taps are staged nine
-// at a time as canonical K-major A operands (8 KB each); Wx (32 x 32T) stays
-// in shared memory for the CTA's lifetime.
-template <int NDIM, int MODE>  // MODE 0: forward epilogue; MODE 1: raw FP32 out
-__global__ void __launch_bounds__(128) net_conv_tc_k(const bf16 *__restrict__ in,
-                                                     const bf16 *__restrict__ Wx,
-                                                     const float *__restrict__ bias, NetShape sh,
-                                                     bf16 *__restrict__ zout, bf16 *__restrict__ outpad,
-                                                     float *__restrict__ outraw, int *status) {
-  constexpr int T = net_taps(NDIM);
-  constexpr int G = 9;
-  constexpr int NG = T / G;
-  constexpr int KB = T * kNetC;
-  constexpr int KCB = KB / 8;
-  constexpr uint32_t idesc = tc_idesc_bf16_f32(128, 32);
-  extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char *sB = sm;                      // 32 x KB
-  unsigned char *sA = sm + 64 * KB;            // G x (128 x 32)
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sA + G * 8192);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-
-  for (int i = tid; i < 32 * KCB; i += 128) {
-    const int n = i / KCB, c = i - n * KCB;
-    *reinterpret_cast<uint4 *>(sB + tc_kmajor_off(n, c * 8, KCB)) =
-        *reinterpret_cast<const uint4 *>(Wx + (int64_t)n * KB + c * 8);
-  }
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(slot, 32);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *slot;
-  uint32_t phase = 0;
-  const int tiles_x = (sh.nx + 127) / 128;
-  const int64_t tiles = (int64_t)sh.batch * sh.nz * sh.ny * tiles_x;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int tx = (int)(tile % tiles_x);
-    int64_t r = tile / tiles_x;
-    const int y = (int)(r % sh.ny);
-    r /= sh.ny;
-    const int z = (int)(r % sh.nz);
-    const int b = (int)(r / sh.nz);
-    const int x0 = tx * 128;
-    for (int g = 0; g < NG; ++g) {
-      for (int i = tid; i < G * 128 * 4; i += 128) {
-        const int c = i & 3, m = (i >> 2) & 127, tg = i >> 9;
-        int oz, oy, ox;
-        net_tap(NDIM, g * G + tg, oz, oy, ox);
-        const int x = min(x0 + m, sh.nx - 1);
-        *reinterpret_cast<uint4 *>(sA + tg * 8192 + tc_kmajor_off(m, c * 8, 4)) =
-            *reinterpret_cast<const uint4 *>(in + sh.ps(b, z, y, x, oz, oy, ox) * kNetC + c * 8);
-      }
-      fence_proxy_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0) {
-        for (int tg = 0; tg < G; ++tg)
-          for (int kk = 0; kk < 2; ++kk) {
-            const int t = g * G + tg;
-            const uint64_t da = tc_smem_desc(sA + tg * 8192 + kk * 256, 128, 512);
-            const uint64_t db = tc_smem_desc(sB + (t * 4 + kk * 2) * 128, 128, KCB * 128);
-            tc_mma_bf16(tmem, da, db, idesc, (g | tg | kk) != 0);
-          }
-        tc_commit(bar);
-      }
-      if (!mbar_wait_bounded(bar, phase)) {
-        report_timeout(status);
-        mbar_wait_bounded(bar, phase);
-      }
-      phase ^= 1u;
-    }
-    tc_fence_after();
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-    const int x = x0 + tid;
-    if (x < sh.nx) {
-      const int64_t pu = sh.u(b, z, y, x);
-      if (MODE == 0) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] += bias[c];
-        if (zout) {
-          uint4 *dz = reinterpret_cast<uint4 *>(zout + pu * kNetC);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) dz[c] = pack8_bf16(v + 8 * c);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = net_gelu(v[c]);
-        store_replicated<NDIM>(outpad, sh, b, z, y, x, v);
-      } else {
-        float4 *d = reinterpret_cast<float4 *>(outraw + pu * kNetC);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) d[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-      }
-    }
-    tc_fence_before();
-  }
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 32);
-}
 
 // -------------------------------------------------- tensor-core wgrad ------
 // dW[t][ci][co] += sum_p a[p + t][ci] * g[p][co] and db[co] += sum_p g[p][co]
@@ -371,6 +213,20 @@ __device__ __forceinline__ void clamp_preimage(int p, int t, int n, int &lo, int
 }
 
 // ------------------------------------------------------------- last layer --
+// z6 = conv(a5, W6) + b6 (32 -> 1 channel) and phi_hat = phi + s z6; in
+// training also the scaled residual's gradient g6 and the loss sum.  A block
+// covers 32 x 8 cells of one z: the 10 x 34 padded pixels (x 3 planes in 3D)
+// it reads are staged once in shared memory with coalesced 16-byte loads
+// (pixel stride 80 bytes: conflict-free 16-byte reads by consecutive lanes),
+// then each thread forms one cell.
+constexpr int kLastTX = 32, kLastTY = 8, kLastPix = 5;  // uint4 per staged pixel (4 + pad)
+
+template <int NDIM>
+__host__ __device__ constexpr int last_smem_bytes() {
+  return (NDIM == 3 ? 3 : 1) * (kLastTY + 2) * (kLastTX + 2) * kLastPix * 16 +
+         net_taps(NDIM) * kNetC * 4;
+}
+
 template <int NDIM, bool TRAIN>
 __global__ void __launch_bounds__(256) net_last_fwd_k(const bf16 *__restrict__ a5pad,
                                                       const float *__restrict__ params, int64_t w_off,
@@ -380,48 +236,73 @@ __global__ void __launch_bounds__(256) net_last_fwd_k(const bf16 *__restrict__ a
                                                       const float *__restrict__ target,
                                                       float *__restrict__ g6, double *loss_acc) {
   constexpr int T = net_taps(NDIM);
-  __shared__ float w[T * kNetC];
+  constexpr int NZR = NDIM == 3 ? 3 : 1;
+  constexpr int RW = kLastTX + 2, RH = kLastTY + 2;
+  extern __shared__ __align__(16) unsigned char lsm[];
+  uint4 *tile = reinterpret_cast<uint4 *>(lsm);                         // [NZR][RH][RW][kLastPix]
+  float *w = reinterpret_cast<float *>(lsm + NZR * RH * RW * kLastPix * 16);  // [T][32]
   __shared__ double red[8];
   for (int i = threadIdx.x; i < T * kNetC; i += blockDim.x) w[i] = params[w_off + i];
-  __syncthreads();
   const float b6 = params[b_off];
-  const int64_t n = sh.cells();
-  const float inv_n = 1.0f / (float)n;
+  const float inv_n = 1.0f / (float)sh.cells();
+  const int tiles_x = (sh.nx + kLastTX - 1) / kLastTX, tiles_y = (sh.ny + kLastTY - 1) / kLastTY;
+  const int64_t items = (int64_t)sh.batch * sh.nz * tiles_y * tiles_x;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   double lsum = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int b, z, y, x;
-    decode_cell<NDIM>(sh, i, b, z, y, x);
-    float acc = b6;
-    for (int t = 0; t < T; ++t) {
-      int oz, oy, ox;
-      net_tap(NDIM, t, oz, oy, ox);
-      const uint4 *src = reinterpret_cast<const uint4 *>(a5pad + sh.ps(b, z, y, x, oz, oy, ox) * kNetC);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float v[8];
-        unpack8_bf16(src[c], v);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc = fmaf(v[e], w[t * kNetC + c * 8 + e], acc);
-      }
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tx = (int)(item % tiles_x);
+    int64_t r = item / tiles_x;
+    const int ty = (int)(r % tiles_y);
+    r /= tiles_y;
+    const int z = (int)(r % sh.nz), b = (int)(r / sh.nz);
+    const int x0 = tx * kLastTX, y0 = ty * kLastTY;
+    __syncthreads();  // the previous item's tile (and w) is complete / released
+    // padded pixels (xp, yp) = (x0 + i, y0 + j), i < RW, j < RH, of planes z .. z+2
+    for (int i = threadIdx.x; i < NZR * RH * RW * 4; i += blockDim.x) {
+      const int c = i & 3;
+      const int q = i >> 2;
+      const int px = q % RW, row = (q / RW) % RH, dz = q / (RW * RH);
+      const int xp = x0 + px, yp = y0 + row;
+      if (xp < sh.px() && yp < sh.py())
+        tile[q * kLastPix + c] = *reinterpret_cast<const uint4 *>(
+            a5pad + (sh.p(b, NDIM == 3 ? z + dz : 0, yp, xp) * kNetC + c * 8));
     }
-    const float ph = phi[i] + scale * acc;
-    phihat[i] = ph;
-    if (TRAIN) {
-      const float r = (ph - target[i]) / scale;
-      g6[i] = 2.0f * r * inv_n;
-      lsum += (double)r * (double)r;
+    __syncthreads();
+    const int x = x0 + lane, y = y0 + wy;
+    if (x < sh.nx && y < sh.ny) {
+      float acc = b6;
+      for (int t = 0; t < T; ++t) {
+        int oz, oy, ox;
+        net_tap(NDIM, t, oz, oy, ox);
+        const int dz = NDIM == 3 ? oz + 1 : 0;
+        const uint4 *src = tile + ((dz * RH + wy + oy + 1) * RW + lane + ox + 1) * kLastPix;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v[8];
+          unpack8_bf16(src[c], v);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc = fmaf(v[e], w[t * kNetC + c * 8 + e], acc);
+        }
+      }
+      const int64_t i = sh.u(b, z, y, x);
+      const float ph = phi[i] + scale * acc;
+      phihat[i] = ph;
+      if (TRAIN) {
+        const float rr = (ph - target[i]) / scale;
+        g6[i] = 2.0f * rr * inv_n;
+        lsum += (double)rr * (double)rr;
+      }
     }
   }
   if (TRAIN) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    if (lane == 0) red[wy] = lsum;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2];
-      atomicAdd(loss_acc, s);
+      double s2 = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s2 += red[w2];
+      atomicAdd(loss_acc, s2);
     }
   }
 }
@@ -610,18 +491,13 @@ static int grid_for(int64_t n, int per_block, int num_sms) {
 }
 
 template <int NDIM>
-static int conv_smem() {
-  return 64 * net_taps(NDIM) * kNetC + 9 * 8192 + 16;
-}
-
-template <int NDIM>
 static cudaError_t setup_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e;
-  e = cudaFuncSetAttribute(net_conv_tc_k<NDIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem<NDIM>());
+  e = cudaFuncSetAttribute(net_last_fwd_k<NDIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, last_smem_bytes<NDIM>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(net_conv_tc_k<NDIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem<NDIM>());
+  e = cudaFuncSetAttribute(net_last_fwd_k<NDIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, last_smem_bytes<NDIM>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(net_wgrad_tc_k<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, WgradGeom<NDIM>::SMEM);
   if (e != cudaSuccess) return e;
@@ -644,21 +520,22 @@ static cudaError_t net_forward_t(const NetBuffers &nb, const NetShape &sh, const
     net_first_fwd_k<NDIM, true><<<grid_for(n, 256, num_sms), 256, 0, s>>>(phi, nb.params, L.w[0], L.b[0], sh, nb.z[0], nb.a[0]);
   else
     net_first_fwd_k<NDIM, false><<<grid_for(n, 256, num_sms), 256, 0, s>>>(phi, nb.params, L.w[0], L.b[0], sh, nullptr, nb.a[0]);
-  const int64_t tiles = (int64_t)sh.batch * sh.nz * sh.ny * ((sh.nx + 127) / 128);
-  const int conv_grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms * 2);
   const int64_t per = (int64_t)kNetC * net_taps(NDIM) * kNetC;
   for (int l = 1; l <= 4; ++l) {
     bf16 *in = nb.a[(l - 1) % (train ? 5 : 2)];
     bf16 *out = nb.a[l % (train ? 5 : 2)];
-    net_conv_tc_k<NDIM, 0><<<conv_grid, 128, conv_smem<NDIM>(), s>>>(
-        in, nb.wf + (l - 1) * per, nb.params + L.b[l], sh, train ? nb.z[l] : nullptr, out, nullptr,
-        nb.status);
+    e = net_conv_rows(0, in, nb.wf + (l - 1) * per, nb.params + L.b[l], sh,
+                      train ? nb.z[l] : nullptr, out, nullptr, nb.status, num_sms, s);
+    if (e != cudaSuccess) return e;
   }
   const bf16 *a5 = nb.a[4 % (train ? 5 : 2)];
+  const int64_t last_items = (int64_t)sh.batch * sh.nz * ((sh.ny + kLastTY - 1) / kLastTY) *
+                             ((sh.nx + kLastTX - 1) / kLastTX);
+  const int last_grid = (int)std::min<int64_t>(last_items, (int64_t)num_sms * 8);
   if (train)
-    net_last_fwd_k<NDIM, true><<<grid_for(n, 256, num_sms), 256, 0, s>>>(a5, nb.params, L.w[5], L.b[5], sh, phi, scale, phihat, target, nb.g6, nb.loss);
+    net_last_fwd_k<NDIM, true><<<last_grid, 256, last_smem_bytes<NDIM>(), s>>>(a5, nb.params, L.w[5], L.b[5], sh, phi, scale, phihat, target, nb.g6, nb.loss);
   else
-    net_last_fwd_k<NDIM, false><<<grid_for(n, 256, num_sms), 256, 0, s>>>(a5, nb.params, L.w[5], L.b[5], sh, phi, scale, phihat, nullptr, nullptr, nullptr);
+    net_last_fwd_k<NDIM, false><<<last_grid, 256, last_smem_bytes<NDIM>(), s>>>(a5, nb.params, L.w[5], L.b[5], sh, phi, scale, phihat, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -670,15 +547,14 @@ static cudaError_t net_backward_t(const NetBuffers &nb, const NetShape &sh, cons
   const int warps_grid = grid_for(n, 8, num_sms);
   net_last_bwd_k<NDIM><<<warps_grid, 256, 0, s>>>(nb.g6, nb.params, L.w[5], sh, nb.z[4], nb.a[4],
                                                  nb.gz[4], nb.grads, L.w[5], L.b[5]);
-  const int64_t tiles = (int64_t)sh.batch * sh.nz * sh.ny * ((sh.nx + 127) / 128);
-  const int conv_grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms * 2);
   const int wgrad_grid = (int)std::min<int64_t>((n + 63) / 64, (int64_t)num_sms);
   const int64_t per = (int64_t)kNetC * net_taps(NDIM) * kNetC;
   for (int l = 4; l >= 1; --l) {
     net_wgrad_tc_k<NDIM><<<wgrad_grid, 128, WgradGeom<NDIM>::SMEM, s>>>(
         nb.a[l - 1], nb.gz[l], sh, nb.grads + L.w[l], nb.grads + L.b[l], nb.status);
-    net_conv_tc_k<NDIM, 1><<<conv_grid, 128, conv_smem<NDIM>(), s>>>(
-        nb.gz[l], nb.wd + (l - 1) * per, nullptr, sh, nullptr, nullptr, nb.raw, nb.status);
+    cudaError_t e = net_conv_rows(1, nb.gz[l], nb.wd + (l - 1) * per, nullptr, sh, nullptr, nullptr,
+                                  nb.raw, nb.status, num_sms, s);
+    if (e != cudaSuccess) return e;
     net_dgrad_finish_k<NDIM><<<warps_grid, 256, net_taps(NDIM) * kNetC * kNetC * 4, s>>>(
         nb.raw, nb.gz[l], nb.params, L.w[l], sh, nb.z[l - 1], nb.gz[l - 1]);
   }

@@ -98,15 +98,76 @@ cudaError_t net_forward(const NetBuffers &nb, const NetShape &sh, const float *p
 cudaError_t net_backward(const NetBuffers &nb, const NetShape &sh, const float *phi, int num_sms,
                          cudaStream_t s);
 cudaError_t net_pack(const NetBuffers &nb, cudaStream_t s);
+// One 32 -> 32 tensor-core convolution over padded activations `in` (mode 0:
+// forward epilogue into zout / outpad; mode 1: raw FP32 into outraw).
+cudaError_t net_conv_rows(int mode, const bf16 *in, const bf16 *Wx, const float *bias,
+                          const NetShape &sh, bf16 *zout, bf16 *outpad, float *outraw, int *status,
+                          int num_sms, cudaStream_t s);
 cudaError_t net_adam(const NetBuffers &nb, float lr, float b1, float b2, float eps, int step,
                      cudaStream_t s);
 
-// tanh-form GELU and its derivative (FP32).
-__device__ __forceinline__ float net_gelu(float x) {
-  const float k = 0.7978845608028654f;  // sqrt(2/pi)
-  const float u = k * fmaf(0.044715f * x, x * x, x);
-  return 0.5f * x * (1.0f + tanhf(u));
+// BF16 packing of 8 FP32 values into one 16-byte word and back.
+__device__ __forceinline__ uint4 pack8_bf16(const float *v) {
+  uint4 u;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+  return u;
 }
+__device__ __forceinline__ void unpack8_bf16(const uint4 &u, float *v) {
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+// Store one cell's 32 activations at its padded position and at the ghost
+// copies it stands for (replicate padding: a boundary cell is also its
+// outside neighbour).
+template <int NDIM>
+__device__ __forceinline__ void store_replicated(bf16 *outpad, const NetShape &sh, int b, int z,
+                                                 int y, int x, const float *a) {
+  uint4 w[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) w[c] = pack8_bf16(a + 8 * c);
+  int xs[3], ys[3], zs[3];
+  int nxs = 0, nys = 0, nzs = 0;
+  xs[nxs++] = x + 1;
+  if (x == 0) xs[nxs++] = 0;
+  if (x == sh.nx - 1) xs[nxs++] = sh.nx + 1;
+  ys[nys++] = y + 1;
+  if (y == 0) ys[nys++] = 0;
+  if (y == sh.ny - 1) ys[nys++] = sh.ny + 1;
+  if (NDIM == 3) {
+    zs[nzs++] = z + 1;
+    if (z == 0) zs[nzs++] = 0;
+    if (z == sh.nz - 1) zs[nzs++] = sh.nz + 1;
+  } else {
+    zs[nzs++] = 0;
+  }
+  for (int iz = 0; iz < nzs; ++iz)
+    for (int iy = 0; iy < nys; ++iy)
+      for (int ix = 0; ix < nxs; ++ix) {
+        uint4 *dst = reinterpret_cast<uint4 *>(outpad + sh.p(b, zs[iz], ys[iy], xs[ix]) * kNetC);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dst[c] = w[c];
+      }
+}
+
+// The forward passes' GELU (tanh form) with the hardware tanh
+// approximation (tanh.approx.f32, relative error about 2^-11, below the BF16
+// rounding of the stored activation).
+__device__ __forceinline__ float net_gelu_fast(float x) {
+  const float k = 0.7978845608028654f;
+  const float u = k * fmaf(0.044715f * x, x * x, x);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return 0.5f * x * (1.0f + t);
+}
+// Its derivative for the backward passes (accurate tanh, FP32).
 __device__ __forceinline__ float net_gelu_grad(float x) {
   const float k = 0.7978845608028654f;
   const float u = k * fmaf(0.044715f * x, x * x, x);

@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMAs --
     if (lane == 0) {
+      const uint64_t a_desc0 = tc_smem_desc(sA, kCvPlane, 128);       // A rows: LBO plane, SBO 8 px
+      const uint64_t b_desc0 = tc_smem_desc(sB, 128, KCB * 128);      // B: canonical K-major
       uint32_t i = 0, o = 0;  // row sets consumed, output rows formed
       bool ok = true;
       for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
@@ -194,18 +196,20 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
           }
           tc_fence_after();
           const uint32_t d = tmem + buf * 32;
-#pragma unroll 1
+          // descriptors: the start-address field is addr >> 4 in the low 14
+          // bits, so a byte offset off (16-byte multiple, inside shared
+          // memory) is + off >> 4 on the base descriptor
+          uint32_t srow[3];
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) srow[dy] = ((base + j + dy) % NS) * (Gm::SET >> 4);
+#pragma unroll
           for (int t = 0; t < T; ++t) {
-            int oz, oy, ox;
-            net_tap(NDIM, t, oz, oy, ox);
-            // row of the set for tap (oz, oy), shifted by ox pixels
-            const int dz = NDIM == 3 ? oz + 1 : 0;
-            const unsigned char *a_row =
-                sA + ((base + j + oy + 1) % NS) * Gm::SET + dz * kCvRow + (ox + 1) * 16;
+            const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, dz = NDIM == 3 ? t / 9 : 0;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t da = tc_smem_desc(a_row + 2 * kk * kCvPlane, kCvPlane, 128);
-              const uint64_t db = tc_smem_desc(sB + (t * 4 + kk * 2) * 128, 128, KCB * 128);
+              const uint64_t da = a_desc0 + srow[oy + 1] +
+                                  (uint32_t)((dz * kCvRow + (ox + 1) * 16 + 2 * kk * kCvPlane) >> 4);
+              const uint64_t db = b_desc0 + (uint32_t)(((t * 4 + kk * 2) * 128) >> 4);
               tc_mma_bf16(d, da, db, idesc, (t | kk) != 0);
             }
           }

@@ -330,8 +330,8 @@ int ac_learned_advance(ac_ctx *ctx, ac_net *net, int64_t jumps, const ac_guard *
 
 /* ------------------------------------------------------ batched mode ---- */
 /* Many independent 2D grids (each its own size, eps, dt and state) advanced
- * together by ONE persistent kernel launch (the paper runs one
- * grid at a time).  Work items are the warp strips x row chunks of the 2D
+ * together by ONE persistent kernel launch (the paper runs one grid at a
+ * time).  Work items are the warp strips x row chunks of the 2D
  * streaming stencil of every instance; a step-block of an item starts once
  * its 3 x 3 neighbourhood has finished the previous one (bounded waits on
  * per-item progress counters), so no grid-wide barrier is needed.  */

@@ -8,7 +8,7 @@ x_i = lower + (i + 1/2) h of Section 2.
 
 Every profile is a tanh of a signed distance divided by sqrt(2) eps (phase
 +1 inside, -1 outside).  Readings where the text is garbled are stated at
-each function and listed in the design doc.
+each function.
 """
 from __future__ import annotations
 

@@ -10,7 +10,7 @@ import paper_2105_09671_gb300 as ac
 NP = {"f64": np.float64, "f32": np.float32, "f16s": np.float16}
 # Tolerances after the stated step counts (max-abs against the FP64 oracle on
 # the same stored initial values): FP64 1e-12 and FP32 1e-5; FP16 storage is
-# judged by relative L2 (1e-3).
+# measured by relative L2 (1e-3).
 TOL_MAXABS = {"f64": 1e-12, "f32": 1e-5}
 TOL_RELL2_F16S = 1e-3
 

@@ -1,0 +1,76 @@
+"""Schedules on the GPU: the autotuner leaves the field untouched and picks a
+schedule the library offers, the tuned choice is reused per size class, and
+graph replay re-captures when the schedule or the tile changes."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_09671_gb300 as ac
+from paper_2105_09671_gb300 import workloads as wl
+
+from gpu_util import assert_parity, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape,dtype", [((48, 64, 80), "f32"), ((130, 200), "f32"),
+                                         ((24, 40, 48), "f64"), ((40, 72, 96), "f16s")])
+def test_autotune_keeps_field_and_steps_correctly(shape, dtype):
+    import torch
+    h = 1.0 / max(shape)
+    eps, dt = 2.5 * h, 0.1 * h * h
+    phi0 = wl.smooth_field(shape, seed=11) + 0.05 * wl.random_field(shape, seed=12)
+    s = torch.cuda.Stream()
+    sim = ac.Simulation(shape, h, eps, dt, dtype=dtype, stream=s)
+    try:
+        sim.load(phi0)
+        before = sim.to_numpy().copy()
+        sim.autotune(8)
+        assert np.array_equal(sim.to_numpy(), before), "autotune changed the field"
+        v, k = sim.schedule()
+        tile = sim.tile()
+        assert v in (ac.AC_VARIANT_DIRECT, ac.AC_VARIANT_STREAM) and 1 <= k <= ac.AC_MAX_K
+        assert 0 <= tile < (ac.AC_NUM_TILES_3D if len(shape) == 3 else 1)
+        sim.step(23)
+        assert sim.status() == ac.AC_OK
+        out = sim.to_numpy().astype(np.float64)
+    finally:
+        sim.close()
+    assert_parity(out, oracle_run(phi0, h, eps, dt, 23, dtype), dtype, f"tuned v{v} k{k} t{tile}")
+    # a second context of the same size class reuses the cached choice
+    sim2 = ac.Simulation(shape, h, eps, dt, dtype=dtype, stream=s)
+    try:
+        sim2.autotune(8)
+        assert sim2.schedule() == (v, k) and sim2.tile() == tile
+    finally:
+        sim2.close()
+
+
+def test_graph_replay_recaptures_on_schedule_and_tile_change():
+    import torch
+    shape = (20, 36, 44)
+    h = 1.0 / 44
+    eps, dt = 2.5 * h, 0.1 * h * h
+    phi0 = wl.smooth_field(shape, seed=5)
+    s = torch.cuda.Stream()
+    sim = ac.Simulation(shape, h, eps, dt, dtype="f32", stream=s)
+    try:
+        sim.load(phi0)
+        sim.set_graph(True)
+        n0 = sim.launch_count()
+        sim.set_schedule(ac.AC_VARIANT_STREAM, 2)
+        sim.set_tile(0)
+        sim.step(6)
+        sim.step(6)                 # replay
+        sim.set_tile(2)
+        sim.step(6)                 # re-captured with tile 2
+        sim.set_schedule(ac.AC_VARIANT_DIRECT, 1)
+        sim.step(6)                 # re-captured with the direct kernel
+        assert sim.status() == ac.AC_OK
+        # 6 steps at depth 2 are launched as 2 + 2 + 1 + 1 (an even count
+        # ends the result in phi), then 6 direct launches
+        assert sim.launch_count() - n0 == 4 + 4 + 4 + 6
+        out = sim.to_numpy().astype(np.float64)
+    finally:
+        sim.close()
+    assert_parity(out, oracle_run(phi0, h, eps, dt, 24, "f32"), "f32", "graph sequence")

@@ -35,6 +35,28 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
   const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
   const int64_t k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
+  // Far from the interface the profile is exactly +-1 (|arg| >= 20, see
+  // tanh_ratio).  An FP32 estimate of the distance decides that for most
+  // cells: its error is below 1e-5 (1 + r + |r0| + |lower| + |c|) (a few
+  // FP32 roundings of values of that size), so beyond that margin the FP64
+  // argument is past 20 on the same side.
+  {
+    const float xf = (float)lx + ((float)i + 0.5f) * (float)h - (float)cx;
+    const float yf = (float)ly + ((float)j + 0.5f) * (float)h - (float)cy;
+    float r2f = xf * xf + yf * yf;
+    if (g.nz > 1) {
+      const float zf = (float)lz + ((float)k + 0.5f) * (float)h - (float)cz;
+      r2f += zf * zf;
+    }
+    const float rf = sqrtf(r2f);
+    const double gap = (double)r0 - (double)rf;
+    const double margin = 1e-5 * (1.0 + (double)rf + fabs(r0) + fabs(lx) + fabs(ly) + fabs(lz) +
+                                  fabs(cx) + fabs(cy) + fabs(cz));
+    if (fabs(gap) >= 20.0 * width + margin) {
+      phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(copysign(1.0, gap));
+      return;
+    }
+  }
   // each operation rounded separately (no contraction), as written
   const double x = __dadd_rn(lx, __dmul_rn(__dadd_rn((double)i, 0.5), h));
   const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));

@@ -69,7 +69,7 @@ static bool same_shape(const NetShape &a, const NetShape &b) {
 // Per-shape buffers: inference keeps two padded activations; training keeps
 // all five, the pre-activations, the padded gradients (zero ghost ring, set
 // once here) and the FP32 scratch.
-static int ensure_shape(ac_net *net, ShapeBufs &s, const NetShape &sh, bool train) {
+static int ensure_shape(ShapeBufs &s, const NetShape &sh, bool train) {
   if (s.valid && same_shape(s.sh, sh) && s.train == train) return AC_OK;
   free_shape(s);
   const size_t act = (size_t)sh.padded_cells() * kNetC * sizeof(bf16);
@@ -240,7 +240,7 @@ extern "C" int ac_net_forward(ac_net *net, const float *phi_dev, float *out_dev,
   NetShape sh;
   int rc = check_shape(net->ndim, batch, nx, ny, nz, &sh);
   if (rc) return rc;
-  rc = ensure_shape(net, net->infer, sh, false);
+  rc = ensure_shape(net->infer, sh, false);
   if (rc) return rc;
   cudaError_t e = net_forward(merged(net, net->infer), sh, phi_dev, (float)scale, out_dev, nullptr,
                               false, net->num_sms, net->stream);
@@ -257,7 +257,7 @@ extern "C" int ac_net_loss_grads(ac_net *net, const float *phi_dev, const float 
   NetShape sh;
   int rc = check_shape(net->ndim, batch, nx, ny, nz, &sh);
   if (rc) return rc;
-  rc = ensure_shape(net, net->train, sh, true);
+  rc = ensure_shape(net->train, sh, true);
   if (rc) return rc;
   const NetBuffers nb = merged(net, net->train);
   NC_CUDA(cudaMemsetAsync(nb.loss, 0, sizeof(double), net->stream));

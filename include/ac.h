@@ -198,10 +198,21 @@ int ac_get_tile(ac_ctx *ctx, int32_t *tile);
  * with CUDA events (about steps_per_trial steps each) and keep the fastest.
  * phi is saved to a temporary device buffer that this call allocates and
  * frees, and restored after every trial, so the field is unchanged.  The
- * choice is cached per (ndim, dtype, log2 of the cell count, device) for
- * the process lifetime; later contexts of the same class reuse it without
- * timing.  Synchronises the stream. */
+ * choice is cached per (ndim, dtype, log2 of the cell count, device model)
+ * for the process lifetime (and in a file, see ac_set_tune_cache); later
+ * contexts of the same class reuse it without timing.  Synchronises the
+ * stream. */
 int ac_autotune(ac_ctx *ctx, int64_t steps_per_trial);
+
+/* Keep autotuning results in a text file as well (one line per choice:
+ * "ac-tune-v1 ndim dtype size_class device variant k tile", device = the
+ * model name and SM count), so that later processes skip the timing:
+ * ac_autotune first looks in the process cache, then in the file, and
+ * appends what it measures.  NULL or "" stops using a file.  Also empties
+ * the process cache.  An unreadable file is treated as empty and a failed
+ * append is ignored (the choice is still used in this process).  Entries
+ * for a schedule this library does not offer are ignored. */
+int ac_set_tune_cache(const char *path);
 
 /* Replay ac_step through a CUDA graph: the first ac_step(n) after enabling
  * (or after the schedule or n changes) captures the whole launch sequence

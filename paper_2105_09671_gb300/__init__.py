@@ -11,7 +11,7 @@ from ._lib import (AC_ERR_CUDA, AC_ERR_INVALID, AC_ERR_NOMEM, AC_ERR_NONFINITE, 
                    AcError, AcGridDesc,
                    EXPORTED, ac_autotune, ac_create, ac_destroy, ac_energy, ac_get_schedule,
                    ac_init_random, ac_init_shape, ac_init_sphere, ac_launch_count, ac_observe, ac_observe_noalloc, ac_phase_volume, ac_set_graph,
-                   ac_set_schedule, ac_set_tile, ac_get_tile, ac_status, ac_step, ac_version,
+                   ac_set_schedule, ac_set_tile, ac_get_tile, ac_set_tune_cache, ac_status, ac_step, ac_version,
                    ac_workspace_bytes, lib,
                    lib_path, make_desc)
 

@@ -29,7 +29,7 @@ AC_SHAPE_DUMBBELL, AC_SHAPE_STAR, AC_SHAPE_TORUS = 1, 2, 3
 EXPORTED = (
     "ac_workspace_bytes", "ac_create", "ac_step", "ac_energy", "ac_phase_volume", "ac_observe",
     "ac_init_sphere", "ac_init_random", "ac_init_shape", "ac_set_schedule", "ac_get_schedule", "ac_set_tile",
-    "ac_get_tile", "ac_autotune",
+    "ac_get_tile", "ac_autotune", "ac_set_tune_cache",
     "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
     "ac_last_error", "ac_version",
     "ac_batch_workspace_bytes", "ac_batch_create", "ac_batch_step", "ac_batch_set_schedule",
@@ -126,6 +126,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_set_tile": [vp, i32],
         "ac_get_tile": [vp, ctypes.POINTER(i32)],
         "ac_autotune": [vp, i64],
+        "ac_set_tune_cache": [ctypes.c_char_p],
         "ac_set_graph": [vp, i32],
         "ac_status": [vp],
         "ac_launch_count": [vp, ctypes.POINTER(i64)],
@@ -261,6 +262,11 @@ def ac_get_tile(ctx: int) -> int:
 
 def ac_autotune(ctx: int, steps_per_trial: int = 64) -> None:
     check(lib().ac_autotune(ctypes.c_void_p(ctx), int(steps_per_trial)))
+
+
+def ac_set_tune_cache(path) -> None:
+    """Keep autotuning choices in a text file as well (None: process cache only)."""
+    check(lib().ac_set_tune_cache(None if path is None else str(path).encode()))
 
 
 def ac_set_graph(ctx: int, enable: bool) -> None:

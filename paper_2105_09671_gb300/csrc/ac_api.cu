@@ -489,8 +489,12 @@ extern "C" int ac_init_random(ac_ctx *c, uint64_t seed, double amplitude) {
 
 // -------------------------------------------------------------- autotune --
 namespace {
+// Tuning results are keyed by grid kind, storage type, size class (log2 of
+// the cell count) and the device model (name and SM count, so that a cache
+// file carries over between processes and between GPUs of the same model).
 struct TuneKey {
-  int ndim, dtype, cls, device;
+  int ndim, dtype, cls;
+  std::string device;
   bool operator<(const TuneKey &o) const {
     return std::tie(ndim, dtype, cls, device) < std::tie(o.ndim, o.dtype, o.cls, o.device);
   }
@@ -500,6 +504,48 @@ struct TuneChoice {
   int variant, k, tile;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
+std::string g_tune_file;  // optional on-disk cache (empty: none)
+
+std::string device_key(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+  std::string name(prop.name);
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  return name + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+// File format, one entry per line:
+//   ac-tune-v1 <ndim> <dtype> <size class> <device> <variant> <k> <tile>
+// Unreadable lines are skipped; the last entry for a key wins.
+bool file_lookup(const TuneKey &key, TuneChoice *out) {
+  if (g_tune_file.empty()) return false;
+  FILE *f = fopen(g_tune_file.c_str(), "r");
+  if (!f) return false;
+  char line[512], tag[32], dev[256];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    int nd, dt, cls, v, k, t;
+    if (sscanf(line, "%31s %d %d %d %255s %d %d %d", tag, &nd, &dt, &cls, dev, &v, &k, &t) != 8)
+      continue;
+    if (strcmp(tag, "ac-tune-v1") != 0) continue;
+    if (nd == key.ndim && dt == key.dtype && cls == key.cls && key.device == dev) {
+      *out = TuneChoice{v, k, t};
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void file_append(const TuneKey &key, const TuneChoice &c) {
+  if (g_tune_file.empty()) return;
+  FILE *f = fopen(g_tune_file.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "ac-tune-v1 %d %d %d %s %d %d %d\n", key.ndim, key.dtype, key.cls, key.device.c_str(),
+          c.variant, c.k, c.tile);
+  fclose(f);
+}
 }  // namespace
 
 static int size_class(const ac_grid_desc &d) {
@@ -510,10 +556,13 @@ static int size_class(const ac_grid_desc &d) {
 extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
   if (steps_per_trial < 1) return fail(AC_ERR_INVALID, "steps_per_trial must be >= 1");
-  const TuneKey key{c->d.ndim, c->d.dtype, size_class(c->d), c->device};
+  const TuneKey key{c->d.ndim, c->d.dtype, size_class(c->d), device_key(c->device)};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
+    TuneChoice fc;
+    if (it == g_tune_cache.end() && file_lookup(key, &fc) && schedule_ok(c, fc.variant, fc.k, fc.tile))
+      it = g_tune_cache.emplace(key, fc).first;
     if (it != g_tune_cache.end()) {
       c->tuned_variant = it->second.variant;
       c->tuned_k = it->second.k;
@@ -563,6 +612,14 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   c->tuned_tile = best_c.tile;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best_c;
+  file_append(key, best_c);
+  return AC_OK;
+}
+
+extern "C" int ac_set_tune_cache(const char *path) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_file = path ? path : "";
+  g_tune_cache.clear();
   return AC_OK;
 }
 

@@ -74,3 +74,43 @@ def test_graph_replay_recaptures_on_schedule_and_tile_change():
     finally:
         sim.close()
     assert_parity(out, oracle_run(phi0, h, eps, dt, 24, "f32"), "f32", "graph sequence")
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    import torch
+    path = tmp_path / "tune.txt"
+    shape = (24, 40, 48)
+    h = 1.0 / 48
+    eps, dt = 2.5 * h, 0.1 * h * h
+    s = torch.cuda.Stream()
+    ac.ac_set_tune_cache(str(path))
+    try:
+        sim = ac.Simulation(shape, h, eps, dt, dtype="f32", stream=s)
+        try:
+            sim.autotune(4)
+            tuned = (sim.schedule(), sim.tile())
+        finally:
+            sim.close()
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1
+        tag, nd, dt_code, cls, dev, v, k, t = lines[0].split()
+        assert tag == "ac-tune-v1" and int(nd) == 3 and int(dt_code) == ac.AC_F32
+        assert (int(v), int(k)) == tuned[0] and int(t) == tuned[1]
+        # a later entry for the same key wins: a new process (emulated by
+        # emptying the process cache) adopts it without timing
+        other = (ac.AC_VARIANT_DIRECT, 1, 0) if tuned[0][0] == ac.AC_VARIANT_STREAM \
+            else (ac.AC_VARIANT_STREAM, 1, 0)
+        with open(path, "a") as f:
+            f.write(f"ac-tune-v1 {nd} {dt_code} {cls} {dev} {other[0]} {other[1]} {other[2]}\n")
+            f.write("not a cache line\n")
+        ac.ac_set_tune_cache(str(path))
+        sim = ac.Simulation(shape, h, eps, dt, dtype="f32", stream=s)
+        try:
+            n0 = sim.launch_count()
+            sim.autotune(4)
+            assert sim.launch_count() == n0  # nothing was timed
+            assert sim.schedule() == other[:2] and sim.tile() == other[2]
+        finally:
+            sim.close()
+    finally:
+        ac.ac_set_tune_cache(None)

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) net_first_fwd_k(const float *__restrict__
                                                        int64_t w_off, int64_t b_off, NetShape sh,
                                                        bf16 *__restrict__ z1, bf16 *__restrict__ a1pad) {
   constexpr int T = net_taps(NDIM);
-  __shared__ float w[T * kNetC], bb[kNetC];
+  __shared__ __align__(16) float w[T * kNetC];
+  __shared__ float bb[kNetC];
   for (int i = threadIdx.x; i < T * kNetC; i += blockDim.x) w[i] = params[w_off + i];
   if (threadIdx.x < kNetC) bb[threadIdx.x] = params[b_off + threadIdx.x];
   __syncthreads();
@@ -67,7 +68,13 @@ __global__ void __launch_bounds__(256) net_first_fwd_k(const float *__restrict__
       const int zz = NDIM == 3 ? min(max(z + oz, 0), sh.nz - 1) : 0;
       const float v = phi[sh.u(b, zz, yy, xx)];
 #pragma unroll
-      for (int c = 0; c < kNetC; ++c) acc[c] = fmaf(v, w[t * kNetC + c], acc[c]);
+      for (int c = 0; c < kNetC; c += 4) {  // 16-byte weight reads (broadcast)
+        const float4 wv = *reinterpret_cast<const float4 *>(w + t * kNetC + c);
+        acc[c] = fmaf(v, wv.x, acc[c]);
+        acc[c + 1] = fmaf(v, wv.y, acc[c + 1]);
+        acc[c + 2] = fmaf(v, wv.z, acc[c + 2]);
+        acc[c + 3] = fmaf(v, wv.w, acc[c + 3]);
+      }
     }
     if (TRAIN) {
       uint4 *dz = reinterpret_cast<uint4 *>(z1 + i * kNetC);
@@ -281,7 +288,13 @@ __global__ void __launch_bounds__(256) net_last_fwd_k(const bf16 *__restrict__ a
           float v[8];
           unpack8_bf16(src[c], v);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) acc = fmaf(v[e], w[t * kNetC + c * 8 + e], acc);
+          for (int e = 0; e < 8; e += 4) {  // 16-byte weight reads (broadcast)
+            const float4 wv = *reinterpret_cast<const float4 *>(w + t * kNetC + c * 8 + e);
+            acc = fmaf(v[e], wv.x, acc);
+            acc = fmaf(v[e + 1], wv.y, acc);
+            acc = fmaf(v[e + 2], wv.z, acc);
+            acc = fmaf(v[e + 3], wv.w, acc);
+          }
         }
       }
       const int64_t i = sh.u(b, z, y, x);

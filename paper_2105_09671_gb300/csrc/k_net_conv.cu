@@ -16,10 +16,11 @@
 //   - warp 0 (one thread) issues the TMA loads into a ring of row sets (the
 //     1 or 3 rows of one y at every needed z), each set on a full / empty
 //     mbarrier pair;
-//   - warp 1 (one thread) issues T x 2 tcgen05.mma (M = 128 pixels, N = 32,
-//     K = 16) per output row into one of four TMEM accumulators and commits
-//     to the accumulator's barrier and to the empty barrier of the set that
-//     this row used for the last time;
+//   - warps 1 and 6 (one thread each, alternate output rows) issue T x 2
+//     tcgen05.mma (M = 128 pixels, N = 32, K = 16) per output row into one
+//     of their two TMEM accumulators and commit to the accumulator's
+//     barrier and to the empty barriers of the sets this issuer no longer
+//     reads (each set is released once by each issuer);
 //   - warps 2..5 read the accumulator (tcgen05.ld, lanes 32 (w % 4) ..),
 //     release it, and run the epilogue: bias, pre-activation store, GELU
 //     (tanh form, hardware tanh approximation) and the store with its
@@ -38,14 +39,15 @@ constexpr int kCvPix = 130;                // 128 outputs + 2 halo columns
 constexpr int kCvPlane = 136 * 16;         // bytes of one 8-channel plane (rows padded to 136)
 constexpr int kCvRow = 4 * kCvPlane;       // one padded input row (32 channels)
 constexpr int kCvBox = 8 * kCvPix * 2;     // bytes of one TMA box
-constexpr int kCvThreads = 192;
+constexpr int kCvThreads = 224;  // TMA warp, 2 MMA warps, 4 epilogue warps
+constexpr int kCvIssuers = 2;    // MMA-issuing warps (alternate output rows)
 
 template <int NDIM>
 struct CvGeom {
   static constexpr int NZ = NDIM == 3 ? 3 : 1;       // rows per set (z - 1, z, z + 1)
   static constexpr int NS = NDIM == 3 ? 6 : 8;       // sets in the ring
   static constexpr int MINB = NDIM == 3 ? 1 : 2;     // CTAs per SM
-  static constexpr int NACC = 4;                      // TMEM accumulators (32 columns each)
+  static constexpr int NACC = 4;                      // TMEM accumulators (2 per issuer)
   static constexpr int T = net_taps(NDIM);
   static constexpr int KB = T * kNetC;                // GEMM K
   static constexpr int KCB = KB / 8;                  // 8-element K chunks of B
@@ -115,13 +117,13 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
     tma_prefetch_desc(&in_map);
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], kCvIssuers);  // each issuer releases every set once
     }
     for (int a = 0; a < NACC; ++a) {
       mbar_init(&accf[a], 1);
       mbar_init(&acce[a], 4);
     }
-    mbar_init(fin, 1);
+    mbar_init(fin, kCvIssuers);
     fence_mbar_init();
     abort_flag = 0;
   }
@@ -174,22 +176,40 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
       for (uint32_t v = i > (uint32_t)NS ? i - NS : 0; v < i; ++v)
         mbar_wait_bounded(&full[v % NS], (v / NS) & 1u);
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 6) {
     // ------------------------------------------------------------- MMAs --
+    // Issuer p takes the item's output rows j = p, p + 2, ...; its k-th row
+    // goes to accumulator p + 2 (k % 2).  It releases set j and j + 1 after
+    // row j (their last use by this issuer); the item's other sets are
+    // released before its first row (those it never reads) or after its
+    // last row (the rest).
+    const int p = warp == 6 ? 1 : 0;
     if (lane == 0) {
       const uint64_t a_desc0 = tc_smem_desc(sA, kCvPlane, 128);       // A rows: LBO plane, SBO 8 px
       const uint64_t b_desc0 = tc_smem_desc(sB, 128, KCB * 128);      // B: canonical K-major
-      uint32_t i = 0, o = 0;  // row sets consumed, output rows formed
+      uint32_t i = 0, kq = 0;  // row sets consumed (CTA), rows formed by this issuer
       bool ok = true;
       for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
         const CvItem it = cv_item(item, sh, tiles_x, nchunk, chunk);
         const uint32_t base = i;
-        for (int j = 0; j < it.nrows && ok; ++j, ++o) {
-          // sets base + j .. base + j + 2 (only the newest is new after j = 0)
-          for (uint32_t k = (j == 0 ? base : base + j + 2); k <= base + j + 2; ++k)
+        const bool had = it.nrows > p;
+        // sets this issuer never reads are released before its first row:
+        // those below it (all of them if it has no row in this item), so
+        // the producer can refill their slots while the other issuer works.
+        // Each release waits for the set to be loaded first: only then has
+        // the slot's previous phase completed, so the arrival counts for
+        // this set and not for the slot's previous occupant.
+        for (int r = 0; r <= it.nrows + 1 && ok; ++r)
+          if (!had || r < p) {
+            const uint32_t k = base + r;
             if (!mbar_wait_bounded(&full[k % NS], (k / NS) & 1u)) ok = false;
-          const uint32_t buf = o % NACC;
-          if (o >= (uint32_t)NACC && !mbar_wait_bounded(&acce[buf], ((o / NACC) - 1) & 1u)) ok = false;
+            else mbar_arrive(&empty[k % NS]);
+          }
+        for (int j = p; j < it.nrows && ok; j += kCvIssuers, ++kq) {
+          for (uint32_t k = base + j; k <= base + j + 2; ++k)
+            if (!mbar_wait_bounded(&full[k % NS], (k / NS) & 1u)) ok = false;
+          const uint32_t buf = p + kCvIssuers * (kq % 2);
+          if (kq >= 2 && !mbar_wait_bounded(&acce[buf], ((kq / 2) - 1) & 1u)) ok = false;
           if (!ok || abort_flag) {
             ok = false;
             break;
@@ -214,12 +234,21 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
             }
           }
           tc_commit(&accf[buf]);
-          tc_commit(&empty[(base + j) % NS]);  // this set's last output row
+          tc_commit(&empty[(base + j) % NS]);      // this issuer's last use of set j
+          tc_commit(&empty[(base + j + 1) % NS]);  // and of set j + 1
         }
         if (!ok) break;
-        // the item's last two sets are no longer needed
-        tc_commit(&empty[(base + it.nrows) % NS]);
-        tc_commit(&empty[(base + it.nrows + 1) % NS]);
+        // the sets above its last row + 1, once that row's MMAs completed
+        // (and, as above, once the set is loaded)
+        if (had) {
+          const int last = it.nrows - 1 - ((it.nrows - 1 - p) % kCvIssuers + kCvIssuers) % kCvIssuers;
+          for (int r = last + 2; r <= it.nrows + 1 && ok; ++r) {
+            const uint32_t k = base + r;
+            if (!mbar_wait_bounded(&full[k % NS], (k / NS) & 1u)) ok = false;
+            else tc_commit(&empty[k % NS]);
+          }
+        }
+        if (!ok) break;
         i = base + it.nrows + 2;
       }
       if (!ok && !abort_flag) {
@@ -233,13 +262,16 @@ __global__ void __launch_bounds__(kCvThreads, CvGeom<NDIM>::MINB)
   } else {
     // -------------------------------------------------------- epilogue --
     const int q = warp & 3;  // TMEM lane quarter of this warp
-    uint32_t o = 0;
+    uint32_t kq[kCvIssuers] = {};  // rows formed so far by each issuer
     bool ok = true;
     for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
       const CvItem it = cv_item(item, sh, tiles_x, nchunk, chunk);
-      for (int j = 0; j < it.nrows; ++j, ++o) {
-        const uint32_t buf = o % NACC;
-        const bool got = mbar_wait_bounded(&accf[buf], (o / NACC) & 1u);
+      for (int j = 0; j < it.nrows; ++j) {
+        const int ip = j % kCvIssuers;  // the issuer of this row and its accumulator
+        const uint32_t buf = ip + kCvIssuers * (kq[ip] % 2);
+        const uint32_t par = (kq[ip] / 2) & 1u;
+        ++kq[ip];
+        const bool got = mbar_wait_bounded(&accf[buf], par);
         if (__any_sync(0xffffffffu, !got || abort_flag)) {  // the warp leaves together
           ok = false;
           break;

@@ -16,22 +16,56 @@ def _stream():
     return torch.cuda.Stream()
 
 
-@pytest.mark.parametrize("ndim,n,pool,iters,drop", [(2, 64, 16, 400, 0.1), (3, 16, 8, 300, 0.8)])
-def test_training_on_plain_trajectories_lowers_the_loss(ndim, n, pool, iters, drop):
-    # the loss spikes whenever a fresh random trajectory (fast spinodal growth)
-    # enters the pool, so compare medians of the first and last windows
+def _held_out_jumps(ndim, n, steps, count, seed):
+    """(inputs, targets) of `count` jumps of the FP64 oracle on n^ndim grids:
+    states of random and tanh-sphere trajectories at several ages, each
+    advanced by `steps` Euler steps; rounded to FP32 like the training data."""
+    h = 1.0 / n
+    eps, dt = 4.0 * h, 0.1 * h * h
+    shape = (n,) * ndim
+    rng = np.random.default_rng(seed)
+    xs, ys = [], []
+    for b in range(count):
+        if b % 2 == 0:
+            phi = oracle.init_random(shape, seed=seed + b)
+        else:
+            phi = oracle.init_sphere(shape, h, float(rng.uniform(0.1, 0.4)), eps)
+        phi = oracle.step(phi, h, eps, dt, steps * int(rng.integers(0, 20)))
+        x = phi.astype(np.float32).astype(np.float64)
+        xs.append(x.astype(np.float32))
+        ys.append(oracle.step(x, h, eps, dt, steps).astype(np.float32))
+    return np.stack(xs), np.stack(ys)
+
+
+@pytest.mark.parametrize("ndim,n,pool,iters,drop", [(2, 64, 16, 400, 0.1), (3, 16, 8, 300, 0.75)])
+def test_training_on_plain_trajectories_lowers_the_held_out_loss(ndim, n, pool, iters, drop):
+    # The training loss itself spikes whenever a fresh trajectory (fast
+    # spinodal growth) enters the pool, so the test measures the loss on a
+    # fixed held-out set of oracle jumps before (the identity jump of the
+    # initial weights) and after training.  Measured on GB300: 2D 2.9e-3 ->
+    # 1.6e-4, 3D (16^3, where eps = 4 h is a quarter of the box) 0.116 -> 0.064.
+    import torch
     s = _stream()
+    steps = 16
+    x, y = _held_out_jumps(ndim, n, steps, 8, seed=900 + ndim)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    nz = n if ndim == 3 else 1
+    scale = steps * 0.1 / 16.0  # steps dt / eps^2 with dt = 0.1 h^2, eps = 4 h
     net = L.ac_net_create(ndim, s.cuda_stream)
     try:
+        torch.cuda.synchronize()
+        before, _ = L.ac_net_loss_grads(net, xd.data_ptr(), yd.data_ptr(), len(x), n, n, nz, scale)
         cfg = L.AcTrainConfig(n=n, eps_cells=4.0, pool=pool, trajectory_jumps=40, iterations=iters,
-                              steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=3)
+                              steps_per_jump=steps, lr=1e-3, lr_final=1e-5, seed=3)
         hist, used = L.ac_net_train(net, cfg)
+        after, _ = L.ac_net_loss_grads(net, xd.data_ptr(), yd.data_ptr(), len(x), n, n, nz, scale)
     finally:
         L.ac_net_destroy(net)
-    k = max(10, iters // 10)
+    print(f"\n{ndim}D held-out loss: identity {before:.3e}, trained {after:.3e}")
     assert used >= pool
     assert np.all(np.isfinite(hist))
-    assert np.median(hist[-k:]) < drop * np.median(hist[:k])
+    assert np.isfinite(after) and after < drop * before
 
 
 def test_rejected_jumps_fall_back_to_the_plain_stepper_exactly():

@@ -51,15 +51,15 @@ constexpr int kS3Tiles = 3;
 template <typename T, int TILE> struct S3Cfg;
 template <int TILE> struct S3Cfg<float, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
-  static constexpr int R = TILE == 2 ? 4 : 2, D = 4, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
 };
 template <int TILE> struct S3Cfg<double, TILE> {
   static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32;
-  static constexpr int R = TILE == 2 ? 4 : 2, D = 4, KMAX = 2, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 2, MINB = TILE == 1 ? 2 : 1;
 };
 template <int TILE> struct S3Cfg<__half, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
-  static constexpr int R = TILE == 2 ? 1 : 2, D = 4, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int R = TILE == 2 ? 1 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
 };
 
 template <typename T, int K, int TILE = 0>
@@ -67,8 +67,10 @@ struct S3Geom {
   using Cfg = S3Cfg<T, TILE>;
   using C = typename Traits<T>::C;
   static constexpr int V = Traits<T>::V;
-  // one step per pass is bound by HBM latency: a deeper TMA ring pays there
-  static constexpr int R = Cfg::R, D = K == 1 ? 6 : Cfg::D, MINB = Cfg::MINB;
+  // D TMA stages; the plane loop is unrolled by U = lcm(3, D) so that every
+  // stage, register-ring slot and level buffer index is a constant.  One
+  // step per pass is bound by HBM latency: a deeper ring pays there.
+  static constexpr int R = Cfg::R, D = K == 1 ? 6 : 3, U = 6 / (D == 6 ? 1 : 2), MINB = Cfg::MINB;
   static constexpr int HX = V * ((K + V - 1) / V);
   static constexpr int OX = Cfg::OX, OY = Cfg::OY;
   static constexpr int TX = OX + 2 * HX, TXV = TX / V;
@@ -78,7 +80,7 @@ struct S3Geom {
   static constexpr int STAGE_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
   static constexpr int LVL_BYTES = TX * TY * (int)sizeof(C);
-  static constexpr int LVL_TOTAL = (K > 1 ? 2 * (K - 1) * LVL_BYTES : 0);
+  static constexpr int LVL_TOTAL = (K > 1 ? 3 * (K - 1) * LVL_BYTES : 0);  // 3 planes per level
   static constexpr int SMEM = D * STAGE_STRIDE + LVL_TOTAL + D * 8 + 16;
   static_assert(NT <= 1024, "tile too large for one CTA");
   static_assert(SMEM <= 227 * 1024, "tile too large for shared memory");
@@ -124,13 +126,13 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
                int tiles_x, int tiles_y, int nzc, int zchunk) {
   using Gm = S3Geom<T, K, TILE>;
   using C = typename Traits<T>::C;
-  constexpr int V = Gm::V, R = Gm::R, TXV = Gm::TXV, TY = Gm::TY, TX = Gm::TX, D = Gm::D;
+  constexpr int V = Gm::V, R = Gm::R, TXV = Gm::TXV, TY = Gm::TY, TX = Gm::TX, D = Gm::D, U = Gm::U;
   constexpr int NSLOT = Gm::NSLOT;
   constexpr int PLANE = TX * TY;  // elements per plane buffer
   extern __shared__ __align__(128) unsigned char smem[];
   // stage s of the TMA ring starts at byte s * STAGE_STRIDE
   auto stage_ptr = [&](int s) { return reinterpret_cast<T *>(smem + s * Gm::STAGE_STRIDE); };
-  C *lvl = reinterpret_cast<C *>(smem + D * Gm::STAGE_STRIDE);  // [K-1][2][TY][TX]
+  C *lvl = reinterpret_cast<C *>(smem + D * Gm::STAGE_STRIDE);  // [K-1][3][TY][TX]
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + D * Gm::STAGE_STRIDE + Gm::LVL_TOTAL);
   volatile int &abort_flag = *reinterpret_cast<int *>(bars + D);
 
@@ -161,7 +163,8 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
   // Level l keeps its last three planes in a ring of register slots: at
   // iteration t slot t%3 holds plane Z+1 (newest), (t+2)%3 plane Z and
   // (t+1)%3 plane Z-1 of the stencil that forms level l+1 of plane Z.  The
-  // plane loop is unrolled by three so that every slot index is a constant.
+  // plane loop is unrolled by U (a multiple of three) so that every slot
+  // index is a constant.
   C ring[K][3][R][V];
 #pragma unroll
   for (int l = 0; l < K; ++l)
@@ -172,7 +175,10 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
 #pragma unroll
         for (int e = 0; e < V; ++e) ring[l][s][i][e] = C(0);
 
-  uint32_t slot = 0;  // planes consumed so far by this CTA: ring position and phase
+  // Every item starts the TMA ring at stage 0 (the previous item consumed
+  // all its loads), so plane t of an item sits in stage t % D; bit s of ph
+  // is the parity of stage s's next completion.
+  uint32_t ph = 0;
   const int items = tiles_x * tiles_y * nzc;
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int tx = item % tiles_x;
@@ -187,9 +193,8 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
 
     if (tid == 0) {
       for (int p = 0; p < D && p < n_in; ++p) {
-        const int s = (int)((slot + p) % D);
-        mbar_arrive_expect_tx(&bars[s], Gm::STAGE_BYTES);
-        tma_load_3d(stage_ptr(s), &src_map, &bars[s], bx, by, lo0 + p);
+        mbar_arrive_expect_tx(&bars[p], Gm::STAGE_BYTES);
+        tma_load_3d(stage_ptr(p), &src_map, &bars[p], bx, by, lo0 + p);
       }
     }
 
@@ -215,20 +220,23 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
     const int64_t goff = (int64_t)(by + r0) * g.pitch + gx0;
 
     auto body = [&]<int P, bool BND>(int t) -> bool {
-      constexpr int SN = P, SB = (P + 2) % 3, SA = (P + 1) % 3;
+      // t % U == P: register-ring slots, TMA stages and level buffers
+      constexpr int SN = P % 3, SB = (P + 2) % 3, SA = (P + 1) % 3;
+      constexpr int SCUR = P % D, SPREV = (P + D - 1) % D;
+      constexpr int LW = P % 3, LR = (P + 2) % 3;
       // Shared-memory reads of this iteration: level 0 reads the stage of
       // plane t-1, level l >= 1 the level-l plane of the previous iteration.
       C ys[K][V], yn[K][V], ev[K][R];
 #pragma unroll
       for (int l = 0; l < K; ++l) {
         if (l == 0) {
-          const T *cb = stage_ptr((int)((slot + t + D - 1) % D));
+          const T *cb = stage_ptr(SPREV);
           ld_vec<T, V>(cb, ysn, ys[0]);
           ld_vec<T, V>(cb, ynn, yn[0]);
 #pragma unroll
           for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
         } else {
-          const C *cb = lvl + ((l - 1) * 2 + ((t + 1) & 1)) * PLANE;
+          const C *cb = lvl + ((l - 1) * 3 + LR) * PLANE;
           ld_vec_c<V>(cb, ysn, ys[l]);
           ld_vec_c<V>(cb, ynn, yn[l]);
 #pragma unroll
@@ -236,10 +244,9 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
         }
       }
       if (!BND || t < n_in) {
-        const uint32_t u = slot + t;
-        const int s = (int)(u % D);
-        if (!mbar_wait_bounded(&bars[s], (u / D) & 1u)) abort_flag = 1;
-        const T *stage = stage_ptr(s);
+        if (!mbar_wait_bounded(&bars[SCUR], (ph >> SCUR) & 1u)) abort_flag = 1;
+        ph ^= 1u << SCUR;
+        const T *stage = stage_ptr(SCUR);
 #pragma unroll
         for (int i = 0; i < R; ++i) ld_vec<T, V>(stage, own + i * TX, ring[0][SN][i]);
       }
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
           if (l + 1 < K) {
 #pragma unroll
             for (int e = 0; e < V; ++e) ring[l + 1 < K ? l + 1 : 0][SN][i][e] = out[e];
-            if (qv) st_vec_c<V>(lvl + (l * 2 + (t & 1)) * PLANE, own + i * TX, out);
+            if (qv) st_vec_c<V>(lvl + (l * 3 + LW) * PLANE, own + i * TX, out);
           } else if (store && st_row[i]) {
             T *d = dst + (int64_t)ZK * plane_stride + goff + (int64_t)i * g.pitch;
             if (st_full) {
@@ -320,20 +327,19 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       if (abort_flag) {
         if (tid == 0) {
           report_timeout(g.status);
-          for (int p = t + 1; p < n_in && p < t + D; ++p) {
-            const uint32_t u = slot + p;
-            mbar_wait_bounded(&bars[u % D], (u / D) & 1u);
-          }
+          // loads in flight: planes t+1 up to D-1 (the prologue's) or t+D-2
+          // (the last refill; this iteration's was not issued)
+          const int last = max(D - 1, t + D - 2);
+          for (int p = t + 1; p < n_in && p <= last; ++p)
+            mbar_wait_bounded(&bars[p % D], (ph >> (p % D)) & 1u);
         }
         return false;
       }
       // the stage of plane t-1 is no longer read: refill it with plane t-1+D
       if (tid == 0 && t >= 1 && t - 1 + D < n_in) {
-        const uint32_t u = slot + t - 1;
-        const int s = (int)(u % D);
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bars[s], Gm::STAGE_BYTES);
-        tma_load_3d(stage_ptr(s), &src_map, &bars[s], bx, by, lo0 + t - 1 + D);
+        mbar_arrive_expect_tx(&bars[SPREV], Gm::STAGE_BYTES);
+        tma_load_3d(stage_ptr(SPREV), &src_map, &bars[SPREV], bx, by, lo0 + t - 1 + D);
       }
       return true;
     };
@@ -345,21 +351,36 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
     const int bnd_lo_end = (lo0 == 0) ? K : -1;
     const int bnd_hi_begin = (hi0 == nz) ? nz - lo0 - 1 : n_iter;
     int t = 0;
-    for (; t + 3 <= n_iter; t += 3) {
-      const bool bnd = yface || (t <= bnd_lo_end) || (t + 2 >= bnd_hi_begin);
+    for (; t + U <= n_iter; t += U) {
+      const bool bnd = yface || (t <= bnd_lo_end) || (t + U - 1 >= bnd_hi_begin);
       if (bnd) {
         if (!body.template operator()<0, true>(t)) return;
         if (!body.template operator()<1, true>(t + 1)) return;
         if (!body.template operator()<2, true>(t + 2)) return;
+        if constexpr (U == 6) {
+          if (!body.template operator()<3, true>(t + 3)) return;
+          if (!body.template operator()<4, true>(t + 4)) return;
+          if (!body.template operator()<5, true>(t + 5)) return;
+        }
       } else {
         if (!body.template operator()<0, false>(t)) return;
         if (!body.template operator()<1, false>(t + 1)) return;
         if (!body.template operator()<2, false>(t + 2)) return;
+        if constexpr (U == 6) {
+          if (!body.template operator()<3, false>(t + 3)) return;
+          if (!body.template operator()<4, false>(t + 4)) return;
+          if (!body.template operator()<5, false>(t + 5)) return;
+        }
       }
     }
+    // the remaining t % U planes (t is a multiple of U here)
     if (t < n_iter && !body.template operator()<0, true>(t++)) return;
     if (t < n_iter && !body.template operator()<1, true>(t++)) return;
-    slot += (uint32_t)n_in;
+    if constexpr (U == 6) {
+      if (t < n_iter && !body.template operator()<2, true>(t++)) return;
+      if (t < n_iter && !body.template operator()<3, true>(t++)) return;
+      if (t < n_iter && !body.template operator()<4, true>(t++)) return;
+    }
   }
 }
 

@@ -18,9 +18,11 @@
 //     consecutive columns of a row group), the two warp-edge lanes read
 //     theirs from shared memory; y neighbours inside the thread's own rows
 //     are registers, the rows above and below its group are shared-memory
-//     reads.  All shared-memory reads of an iteration were published before
-//     its barrier, so they are issued together at its start, ahead of the
-//     wait for the new input plane;
+//     reads.  The reads of level 0 (the previous input plane's stage) are
+//     issued at the start of an iteration, ahead of the wait for the new
+//     plane; those of level l >= 1 right before level l is formed, which
+//     spreads the iteration's shared-memory traffic instead of issuing it
+//     in one burst after the barrier;
 //   - zero-Neumann ghosts (Section 2) are clamps at the current level: a
 //     neighbour across a domain face is the boundary cell itself.  y faces
 //     are clamped shared-memory offsets and, inside a row group, a select
@@ -224,8 +226,8 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       constexpr int SN = P % 3, SB = (P + 2) % 3, SA = (P + 1) % 3;
       constexpr int SCUR = P % D, SPREV = (P + D - 1) % D;
       constexpr int LW = P % 3, LR = (P + 2) % 3;
-      // Shared-memory reads of this iteration: level 0 reads the stage of
-      // plane t-1, level l >= 1 the level-l plane of the previous iteration.
+      // Shared-memory reads of level 0: the stage of plane t-1 (level l >= 1
+      // reads the level-l plane of the previous iteration in its own turn).
       C ys[K][V], yn[K][V], ev[K][R];
 #pragma unroll
       for (int l = 0; l < K; ++l) {
@@ -235,12 +237,6 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
           ld_vec<T, V>(cb, ynn, yn[0]);
 #pragma unroll
           for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
-        } else {
-          const C *cb = lvl + ((l - 1) * 3 + LR) * PLANE;
-          ld_vec_c<V>(cb, ysn, ys[l]);
-          ld_vec_c<V>(cb, ynn, yn[l]);
-#pragma unroll
-          for (int i = 0; i < R; ++i) ev[l][i] = esm ? cb[eoff + i * TX] : C(0);
         }
       }
       if (!BND || t < n_in) {
@@ -252,6 +248,13 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       }
 #pragma unroll
       for (int l = 0; l < K; ++l) {
+        if (l > 0) {
+          const C *cb = lvl + ((l - 1) * 3 + LR) * PLANE;
+          ld_vec_c<V>(cb, ysn, ys[l]);
+          ld_vec_c<V>(cb, ynn, yn[l]);
+#pragma unroll
+          for (int i = 0; i < R; ++i) ev[l][i] = esm ? cb[eoff + i * TX] : C(0);
+        }
         const int Z = lo0 + t - (l + 1);  // plane of level l+1 formed now
         if constexpr (BND) {
           if (Z == 0) {                   // ghost below the bottom face
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
             if (qv) st_vec_c<V>(lvl + (l * 3 + LW) * PLANE, own + i * TX, out);
           } else if (store && st_row[i]) {
             T *d = dst + (int64_t)ZK * plane_stride + goff + (int64_t)i * g.pitch;
-            if (st_full) {
+            if (FASTX || st_full) {  // (FASTX: nx % V == 0, every vector is whole)
               *reinterpret_cast<uint4 *>(d) = pack16<T>(out);
             } else {
 #pragma unroll

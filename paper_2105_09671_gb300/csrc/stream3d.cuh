@@ -12,7 +12,7 @@
 //   - a thread owns R vertically adjacent 16-byte vectors (one column of R
 //     rows) and keeps, for each, the last three planes of every level in a
 //     ring of registers (the z neighbours); levels 1..k-1 also publish their
-//     newest plane in shared memory (double buffered) for the x/y
+//     newest plane in shared memory (three buffers) for the x/y
 //     neighbours of others;
 //   - x neighbours come from the adjacent lane by warp shuffle (lanes own
 //     consecutive columns of a row group), the two warp-edge lanes read

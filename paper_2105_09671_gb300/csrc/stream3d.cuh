@@ -54,14 +54,17 @@ template <typename T, int TILE> struct S3Cfg;
 template <int TILE> struct S3Cfg<float, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int DK = TILE == 0 ? 6 : 3;  // TMA stages at k >= 2
 };
 template <int TILE> struct S3Cfg<double, TILE> {
   static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 2, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int DK = 3;
 };
 template <int TILE> struct S3Cfg<__half, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 1 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
+  static constexpr int DK = 3;
 };
 
 template <typename T, int K, int TILE = 0>
@@ -69,10 +72,7 @@ struct S3Geom {
   using Cfg = S3Cfg<T, TILE>;
   using C = typename Traits<T>::C;
   static constexpr int V = Traits<T>::V;
-  // D TMA stages; the plane loop is unrolled by U = lcm(3, D) so that every
-  // stage, register-ring slot and level buffer index is a constant.  One
-  // step per pass is bound by HBM latency: a deeper ring pays there.
-  static constexpr int R = Cfg::R, D = K == 1 ? 6 : 3, U = 6 / (D == 6 ? 1 : 2), MINB = Cfg::MINB;
+  static constexpr int R = Cfg::R, MINB = Cfg::MINB;
   static constexpr int HX = V * ((K + V - 1) / V);
   static constexpr int OX = Cfg::OX, OY = Cfg::OY;
   static constexpr int TX = OX + 2 * HX, TXV = TX / V;
@@ -83,6 +83,16 @@ struct S3Geom {
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
   static constexpr int LVL_BYTES = TX * TY * (int)sizeof(C);
   static constexpr int LVL_TOTAL = (K > 1 ? 3 * (K - 1) * LVL_BYTES : 0);  // 3 planes per level
+  // D TMA stages (3 or 6; the planes in flight hide HBM latency): 6 at
+  // k = 1, else per type and tile as measured on GB300 at 512^3 (six pay
+  // for the FP32 128 x 32 tile, +5 % at k = 2, and cost elsewhere, where
+  // the twice-unrolled plane loop outgrows the instruction cache).  The
+  // plane loop is unrolled by U = lcm(3, D) so that every stage,
+  // register-ring slot and level buffer index is a constant.
+  static constexpr bool FITS6 = 6 * STAGE_STRIDE + LVL_TOTAL + 6 * 8 + 16 <= 227 * 1024;
+  static constexpr int D = K == 1 ? 6 : (Cfg::DK == 6 && FITS6 ? 6 : 3);
+  static constexpr int U = D == 6 ? 6 : 3;
+  static_assert(D == 3 || D == 6, "stages");
   static constexpr int SMEM = D * STAGE_STRIDE + LVL_TOTAL + D * 8 + 16;
   static_assert(NT <= 1024, "tile too large for one CTA");
   static_assert(SMEM <= 227 * 1024, "tile too large for shared memory");

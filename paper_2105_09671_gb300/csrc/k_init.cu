@@ -23,9 +23,19 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counte
 // < 2 e^{-39.9} < 2^-54 (half an ulp below 1), so the correctly rounded value
 // is exactly +-1.  Most cells of a tanh profile lie there and skip the FP64
 // division and tanh.
-__device__ __forceinline__ double tanh_ratio(double num, double w) {
-  return fabs(num) >= __dmul_rn(20.0, w) ? copysign(1.0, num) : tanh(__ddiv_rn(num, w));
+__device__ __forceinline__ double tanh_ratio(double num, double w, double sat = 20.0) {
+  return fabs(num) >= __dmul_rn(sat, w) ? copysign(1.0, num) : tanh(__ddiv_rn(num, w));
 }
+
+// Where a profile value is stored as it is (the sphere), the short-cut can
+// start where tanh rounds to +-1 in the storage type: 1 - tanh a < 2 e^{-2a}
+// is below half the spacing under 1 (2^-25 for FP32, 2^-12 for FP16) from
+// a = 9.5 (2 e^{-19} = 1.1e-8) and a = 6 (2 e^{-12} = 1.2e-5) on, so the
+// FP64 value there rounds to exactly +-1 too and the stored field is the
+// same.  (Shapes that add several tanh terms keep the FP64 threshold.)
+template <typename T> struct SatArg { static constexpr double value = 20.0; };
+template <> struct SatArg<float> { static constexpr double value = 9.5; };
+template <> struct SatArg<__half> { static constexpr double value = 6.0; };
 
 template <typename T>
 __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, double lx, double ly,
@@ -35,11 +45,12 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
   const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
   const int64_t k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
-  // Far from the interface the profile is exactly +-1 (|arg| >= 20, see
-  // tanh_ratio).  An FP32 estimate of the distance decides that for most
-  // cells: its error is below 1e-5 (1 + r + |r0| + |lower| + |c|) (a few
-  // FP32 roundings of values of that size), so beyond that margin the FP64
-  // argument is past 20 on the same side.
+  constexpr double kSat = SatArg<T>::value;
+  // Far from the interface the stored profile is exactly +-1 (|arg| >= kSat,
+  // see SatArg).  An FP32 estimate of the distance decides that for most
+  // cells, in FP32 throughout: its error is below 1e-6 (1 + r + |r0| +
+  // |lower| + |c|) (a few FP32 roundings of values of that size), so beyond
+  // twenty times that margin the FP64 argument is past kSat on the same side.
   {
     const float xf = (float)lx + ((float)i + 0.5f) * (float)h - (float)cx;
     const float yf = (float)ly + ((float)j + 0.5f) * (float)h - (float)cy;
@@ -49,11 +60,11 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
       r2f += zf * zf;
     }
     const float rf = sqrtf(r2f);
-    const double gap = (double)r0 - (double)rf;
-    const double margin = 1e-5 * (1.0 + (double)rf + fabs(r0) + fabs(lx) + fabs(ly) + fabs(lz) +
-                                  fabs(cx) + fabs(cy) + fabs(cz));
-    if (fabs(gap) >= 20.0 * width + margin) {
-      phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(copysign(1.0, gap));
+    const float gapf = (float)r0 - rf;
+    const float margin = 2e-5f * (1.0f + rf + fabsf((float)r0) + fabsf((float)lx) + fabsf((float)ly) +
+                                  fabsf((float)lz) + fabsf((float)cx) + fabsf((float)cy) + fabsf((float)cz));
+    if (fabsf(gapf) >= (float)(kSat * width) + margin) {
+      phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(gapf > 0.0f ? 1.0 : -1.0);
       return;
     }
   }
@@ -67,7 +78,7 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
     const double dz = __dsub_rn(z, cz);
     r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
   }
-  const double v = tanh_ratio(__dsub_rn(r0, __dsqrt_rn(r2)), width);
+  const double v = tanh_ratio(__dsub_rn(r0, __dsqrt_rn(r2)), width, kSat);
   phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
 }
 

@@ -33,8 +33,9 @@
 //     vector width (FASTX), else per element;
 //   - only level k inside the tile interior and the chunk's own planes is
 //     written; the halo cells computed on the way are discarded.
-// One __syncthreads per plane; persistent CTAs loop over (tile, z-chunk)
-// items.
+// One CTA barrier per plane (__syncthreads_or, which also tells every
+// thread whether any bounded wait expired); persistent CTAs loop over
+// (tile, z-chunk) items.
 #pragma once
 
 #include <algorithm>
@@ -93,7 +94,7 @@ struct S3Geom {
   static constexpr int D = K == 1 ? 6 : (Cfg::DK == 6 && FITS6 ? 6 : 3);
   static constexpr int U = D == 6 ? 6 : 3;
   static_assert(D == 3 || D == 6, "stages");
-  static constexpr int SMEM = D * STAGE_STRIDE + LVL_TOTAL + D * 8 + 16;
+  static constexpr int SMEM = D * STAGE_STRIDE + LVL_TOTAL + D * 8;  // + the stage barriers
   static_assert(NT <= 1024, "tile too large for one CTA");
   static_assert(SMEM <= 227 * 1024, "tile too large for shared memory");
   static_assert(TY <= 256 && TX <= 256, "TMA box limits");
@@ -146,14 +147,12 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
   auto stage_ptr = [&](int s) { return reinterpret_cast<T *>(smem + s * Gm::STAGE_STRIDE); };
   C *lvl = reinterpret_cast<C *>(smem + D * Gm::STAGE_STRIDE);  // [K-1][3][TY][TX]
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + D * Gm::STAGE_STRIDE + Gm::LVL_TOTAL);
-  volatile int &abort_flag = *reinterpret_cast<int *>(bars + D);
 
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     tma_prefetch_desc(&src_map);
     for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
-    abort_flag = 0;
   }
   __syncthreads();
 
@@ -249,9 +248,10 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
           for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
         }
       }
+      bool ok = true;
       if (!BND || t < n_in) {
-        if (!mbar_wait_bounded(&bars[SCUR], (ph >> SCUR) & 1u)) abort_flag = 1;
-        ph ^= 1u << SCUR;
+        ok = mbar_wait_bounded(&bars[SCUR], (ph >> SCUR) & 1u);
+        if (ok) ph ^= 1u << SCUR;  // (an expired wait keeps the parity for the drain)
         const T *stage = stage_ptr(SCUR);
 #pragma unroll
         for (int i = 0; i < R; ++i) ld_vec<T, V>(stage, own + i * TX, ring[0][SN][i]);
@@ -323,11 +323,15 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
 #pragma unroll
             for (int e = 0; e < V; ++e) ring[l + 1 < K ? l + 1 : 0][SN][i][e] = out[e];
             if (qv) st_vec_c<V>(lvl + (l * 3 + LW) * PLANE, own + i * TX, out);
-          } else if (store && st_row[i]) {
+          } else {
+            // the address is formed by every thread and only the store is
+            // predicated (one predicated 16-byte store, no branch)
             T *d = dst + (int64_t)ZK * plane_stride + goff + (int64_t)i * g.pitch;
+            const bool sv = store && st_row[i];
             if (FASTX || st_full) {  // (FASTX: nx % V == 0, every vector is whole)
-              *reinterpret_cast<uint4 *>(d) = pack16<T>(out);
-            } else {
+              const uint4 pk = pack16<T>(out);
+              if (sv) *reinterpret_cast<uint4 *>(d) = pk;
+            } else if (sv) {
 #pragma unroll
               for (int e = 0; e < V; ++e)
                 if (gx0 + e < nx) d[e] = from_c<T>(out[e]);
@@ -336,14 +340,16 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
         }
       }
 
-      __syncthreads();
-      if (abort_flag) {
+      // the plane barrier, which also tells every thread whether any
+      // thread's wait expired
+      if (__syncthreads_or(!ok)) {
         if (tid == 0) {
           report_timeout(g.status);
-          // loads in flight: planes t+1 up to D-1 (the prologue's) or t+D-2
-          // (the last refill; this iteration's was not issued)
+          // loads that may be in flight: from plane t (t + 1 if thread 0
+          // saw it land) up to D-1 (the prologue's) or t+D-2 (the last
+          // refill; this iteration's was not issued)
           const int last = max(D - 1, t + D - 2);
-          for (int p = t + 1; p < n_in && p <= last; ++p)
+          for (int p = ok ? t + 1 : t; p < n_in && p <= last; ++p)
             mbar_wait_bounded(&bars[p % D], (ph >> (p % D)) & 1u);
         }
         return false;

@@ -6,12 +6,21 @@
 //   vol  = sum_cells (1 + phi) / 2
 //
 // The host turns these into E_h = h^d (bulk / eps^2 + grad / (2 h^2)) and
-// V = h^d vol.  Every term is formed and accumulated in FP64 (sums over
-// 1e8 cells need it).  The result is deterministic: a fixed grid of blocks
-// each reduces a fixed set of rows in a fixed order, and a single block adds
-// the per-block partials in index order.
+// V = h^d vol.  Sums over 1e8 cells need FP64 accumulation.  FP64 fields
+// form every term in FP64.  FP32 / FP16 fields hold values that are exact in
+// FP32, and GB300 runs FP32 at many times its FP64 rate, so there the terms
+// are formed in float-float arithmetic (an unevaluated FP32 pair hi + lo):
+// TwoSum (Knuth; Moller 1965) and the FMA form of TwoProduct (Dekker 1971;
+// Ogita, Rump, Oishi 2005) give p^2 and phi_a - phi_b exactly, the squares
+// keep ~46 bits, and each lane adds its terms in float-float over groups of
+// kFFGroup cells before the group's sum is added in FP64 (relative error of
+// the sums ~1e-15, against the FP64 oracle's ~1e-16).  The result is
+// deterministic: a fixed grid of blocks each reduces a fixed set of rows in
+// a fixed order, and a single block adds the per-block partials in index
+// order.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -22,6 +31,33 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Error-free transformations in FP32 (every operation rounded as written).
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (h + l)^2 for |l| <= ulp(h): h^2 exactly plus 2 h l
+__device__ __forceinline__ FF square_ff(float h, float l) {
+  FF r = two_prod(h, h);
+  r.l = __fmaf_rn(__fmul_rn(2.0f, h), l, r.l);
+  return r;
+}
+// acc += t (t a float-float term)
+__device__ __forceinline__ void add_ff(FF &acc, FF t) {
+  const FF s = two_sum(acc.h, t.h);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, t.l));
+}
+constexpr int kFFGroup = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) observe_partial(const T *__restrict__ phi, GridParams g,
@@ -37,15 +73,52 @@ __global__ void __launch_bounds__(256) observe_partial(const T *__restrict__ phi
     const int64_t j = r % g.ny, k = r / g.ny;
     const T *row = phi + k * plane + j * g.pitch;
     const bool has_up = j + 1 < g.ny, has_front = k + 1 < g.nz;
-    for (int64_t i = lane; i < g.nx; i += 32) {
-      const double p = (double)to_c(row[i]);
-      if (!isfinite(p)) bad += 1.0;
-      const double q = p * p - 1.0;
-      bulk += 0.25 * q * q;
-      vol += 0.5 * (1.0 + p);
-      if (i + 1 < g.nx) { double d = (double)to_c(row[i + 1]) - p; grad += d * d; }
-      if (has_up) { double d = (double)to_c(row[i + g.pitch]) - p; grad += d * d; }
-      if (has_front) { double d = (double)to_c(row[i + plane]) - p; grad += d * d; }
+    if constexpr (std::is_same_v<T, double>) {
+      for (int64_t i = lane; i < g.nx; i += 32) {
+        const double p = row[i];
+        if (!isfinite(p)) bad += 1.0;
+        const double q = p * p - 1.0;
+        bulk += 0.25 * q * q;
+        vol += 0.5 * (1.0 + p);
+        if (i + 1 < g.nx) { double d = row[i + 1] - p; grad += d * d; }
+        if (has_up) { double d = row[i + g.pitch] - p; grad += d * d; }
+        if (has_front) { double d = row[i + plane] - p; grad += d * d; }
+      }
+    } else {
+      for (int64_t i0 = lane; i0 < g.nx; i0 += 32 * kFFGroup) {
+        FF b{0.f, 0.f}, gr{0.f, 0.f}, sp{0.f, 0.f};
+        int cnt = 0;
+#pragma unroll 4
+        for (int u = 0; u < kFFGroup; ++u) {
+          const int64_t i = i0 + 32 * u;
+          if (i >= g.nx) break;
+          const float p = to_c(row[i]);
+          if (!isfinite(p)) bad += 1.0;
+          ++cnt;
+          // (p^2 - 1)^2: p^2 = p2.h + p2.l exactly, q = p^2 - 1 to ~48 bits
+          const FF p2 = two_prod(p, p);
+          FF q = two_sum(p2.h, -1.0f);
+          q.l = __fadd_rn(q.l, p2.l);
+          add_ff(b, square_ff(q.h, q.l));
+          add_ff(sp, FF{p, 0.f});
+          // (phi_a - p)^2 over the faces to the +x, +y, +z neighbours
+          if (i + 1 < g.nx) {
+            const FF d = two_sum(to_c(row[i + 1]), -p);
+            add_ff(gr, square_ff(d.h, d.l));
+          }
+          if (has_up) {
+            const FF d = two_sum(to_c(row[i + g.pitch]), -p);
+            add_ff(gr, square_ff(d.h, d.l));
+          }
+          if (has_front) {
+            const FF d = two_sum(to_c(row[i + plane]), -p);
+            add_ff(gr, square_ff(d.h, d.l));
+          }
+        }
+        bulk += 0.25 * ((double)b.h + (double)b.l);
+        grad += (double)gr.h + (double)gr.l;
+        vol += 0.5 * (double)cnt + 0.5 * ((double)sp.h + (double)sp.l);
+      }
     }
   }
   __shared__ double red[4][kWarps];

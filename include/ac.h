@@ -112,7 +112,10 @@ int ac_step(ac_ctx *ctx, int64_t n);
 /* Discrete Ginzburg-Landau energy of the current phi, summed in FP64:
  *   E_h = h^d [ sum_cells F(phi)/eps^2 + 1/2 sum_interior faces ((phi_a - phi_b)/h)^2 ]
  * (not defined in the paper; its gradient is -h^d times the right-hand side
- * of Eq. pytorchACeq, so the scheme decreases it).  Synchronises the stream.
+ * of Eq. pytorchACeq, so the scheme decreases it).  The per-cell terms are
+ * formed in FP64 for FP64 storage and in float-float arithmetic (~46 bits;
+ * the stored values are exact in FP32) for FP32 / FP16 storage, so the
+ * result is within ~1e-15 relative of FP64 terms.  Synchronises the stream.
  * Returns AC_ERR_NONFINITE (and still writes *out) if phi holds NaN/Inf. */
 int ac_energy(ac_ctx *ctx, double *out);
 

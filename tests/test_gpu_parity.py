@@ -74,6 +74,24 @@ def test_ragged_shapes_every_schedule(shape, dtype):
             assert_parity(out, ref, dtype, f"{shape} {dtype} v{variant} k{k} t{tile} n{n}")
 
 
+def test_3d_plane_counts_cover_every_unrolled_remainder():
+    """nz = 1..13 on a one-tile xy grid: the plane loop (unrolled by 3 or 6)
+    ends on every remainder, items have fewer planes than TMA stages, and
+    from nz = 8 on the grid splits into several z-chunks."""
+    from paper_2105_09671_gb300 import _lib as L
+    for nz in range(1, 14):
+        shape = (nz, 20, 24)
+        h, eps, dt = _params(shape)
+        phi0 = wl.smooth_field(shape, seed=nz) + 0.05 * wl.random_field(shape, seed=nz + 1)
+        for variant, k, tile in schedules(3, "f32"):
+            if variant != L.AC_VARIANT_STREAM:
+                continue
+            n = 2 * k + 1
+            ref = oracle_run(phi0, h, eps, dt, n, "f32")
+            out = gpu_run(phi0, h, eps, dt, n, "f32", variant, k, tile)
+            assert_parity(out, ref, "f32", f"nz {nz} k{k} t{tile}")
+
+
 @pytest.mark.parametrize("shape", [(37, 45), (7, 19, 23)])
 def test_f16_storage_ragged(shape):
     h, eps, dt = _params(shape)

@@ -182,18 +182,25 @@ enum {
 int ac_set_schedule(ac_ctx *ctx, int32_t variant, int32_t k);
 int ac_get_schedule(ac_ctx *ctx, int32_t *variant, int32_t *k);
 
-/* Tile shape of the 3D streaming kernel (the xy block each CTA streams
- * along z; the temporal blocking of Section 3.2 recomputes a halo of k cells
- * around it).  Tiles 0..AC_NUM_TILES_3D-1 (FP32 / FP16 storage; FP64 tiles
- * are half as wide in x):
+/* Tile shape of the streaming kernel.  3D: the xy block each CTA streams
+ * along z (temporal blocking recomputes a halo of k cells around it),
+ * tiles 0..AC_NUM_TILES_3D-1 (FP32 / FP16 storage; FP64 tiles are half as
+ * wide in x):
  *   0: 128 x 32 outputs, two rows per thread
  *   1: 128 x 16 outputs, two rows per thread, several CTAs per SM
  *   2: 128 x 32 outputs, four rows per thread (FP16 storage: one)
- * AC_TILE_AUTO (-1) restores the autotuned or default choice.  2D grids
- * accept tile 0 only (AC_ERR_UNSUPPORTED otherwise).  The result of a step
+ * 2D: the width of the column strip each warp streams along y, tiles
+ * 0..AC_NUM_TILES_2D-1:
+ *   0: one 16-byte vector per lane (FP32 / FP16 storage: 4 / 8 cells;
+ *      FP64: two vectors, 4 cells), depths up to 8 (FP16 storage: 6)
+ *   1: FP32 only, two vectors per lane (8 cells, 256-cell strips; half
+ *      the shuffles and the strip-halo share per cell), depths up to 6
+ * AC_TILE_AUTO (-1) restores the autotuned or default choice; a tile the
+ * grid kind does not offer is AC_ERR_UNSUPPORTED.  The result of a step
  * does not depend on the tile. */
 #define AC_TILE_AUTO (-1)
 #define AC_NUM_TILES_3D 3
+#define AC_NUM_TILES_2D 2
 int ac_set_tile(ac_ctx *ctx, int32_t tile);
 int ac_get_tile(ac_ctx *ctx, int32_t *tile);
 
@@ -263,13 +270,45 @@ int ac_tc_gemm_bf16_n32(const void *a_dev, const void *b_dev, float *d_dev, int6
  * Fields: FP32, contiguous [batch][nz][ny][nx] device arrays. */
 typedef struct ac_net ac_net; /* opaque */
 
+/* The guard every learned jump phi -> phi_hat must pass; a rejected jump is
+ * replaced by n plain steps.  Checks, all on the device:
+ *   energy    E(phi_hat) <= E(phi) (1 + energy_rtol)  (the scheme decreases
+ *             the discrete energy; FP64 reduction);
+ *   max-norm  max |phi_hat| <= max_abs (the scheme keeps |phi| <= 1);
+ *   residual  max |phi_hat - phi - n dt RHS(phi)| <= residual_tol, RHS the
+ *             bracket of Eq. (pytorchACeq): a one-shot Euler estimate of the
+ *             jump, a coarse consistency check (ac_net_calibrate_guard sets
+ *             residual_tol from the plain stepper's own residual);
+ *   spot      the local error against the plain stepper itself: on
+ *             spot_samples boxes of spot_size^d cells (plus an n-cell margin)
+ *             at pseudo-random places (spot_seed, advanced every jump) the
+ *             plain stepper's n-step result is computed exactly (the n-step
+ *             domain of dependence fits in the box) and compared with
+ *             phi_hat: accept if sqrt(sum (phi_hat - ref)^2 / sum ref^2)
+ *             <= spot_rtol over the checked cells.
+ * A tolerance <= 0 disables its check.  spot_samples / spot_size = 0 take
+ * the defaults 64 / 32 (2D) and 16 / 8 (3D). */
 typedef struct {
   int32_t steps_per_jump; /* n: Euler steps one learned jump stands for            */
   double energy_rtol;     /* accept if E(phi_hat) <= E(phi) (1 + energy_rtol)       */
   double max_abs;         /* accept if max |phi_hat| <= max_abs                     */
-  double residual_tol;    /* accept if max |phi_hat - phi - n dt RHS(phi)| <= this
-                             (<= 0 disables the check)                              */
+  double residual_tol;    /* accept if max |phi_hat - phi - n dt RHS(phi)| <= this  */
+  double spot_rtol;       /* accept if the spot-checked relative L2 error <= this   */
+  int32_t spot_samples;   /* boxes checked per jump (0 = default)                   */
+  int32_t spot_size;      /* checked cells per box side (0 = default)               */
+  uint64_t spot_seed;     /* places of the boxes (jump j uses spot_seed + j)        */
 } ac_guard;
+
+/* What ac_learned_advance saw: jumps tried, rejections by cause (a jump can
+ * fail several checks; each failed check is counted), and the largest
+ * values of the checked quantities over all jumps (accepted or not). */
+typedef struct {
+  int64_t jumps, fallbacks;
+  int64_t rejected_nonfinite, rejected_energy, rejected_max_abs, rejected_residual, rejected_spot;
+  double max_residual;      /* largest max |phi_hat - phi - n dt RHS(phi)|      */
+  double max_spot_rel;      /* largest spot-checked relative L2 error           */
+  double max_spot_abs;      /* largest spot-checked max |phi_hat - ref|         */
+} ac_learned_report;
 
 int ac_net_param_count(int32_t ndim, int64_t *out);
 /* ndim 2 or 3; weights start He-normal (std sqrt(2 / fan_in), seed 0) with
@@ -332,15 +371,52 @@ int ac_net_train(ac_net *net, const ac_train_config *cfg, double *loss_history,
  * threshold on jumps of the plain stepper.  Synchronises. */
 int ac_jump_residual(ac_ctx *ctx, const float *phat_dev, int32_t steps, double out[2]);
 
+/* The guard's spot check on its own (FP32 context, phat_dev laid out as
+ * the context's field, any pitch): compares phat_dev with the plain
+ * stepper's `steps`-step result from the context's phi on `samples` boxes
+ * of size^d checked cells (0 = the ac_guard defaults) placed by `seed`.
+ * out[0] = max |phat - ref|, out[1] = relative L2 error over the checked
+ * cells, out[2] = cells checked.  The reference values are the plain
+ * stepper's own FP32 results bit for bit, so a jump made by ac_step gives 0.
+ * Allocates and frees a scratch buffer; synchronises. */
+int ac_jump_spot_check(ac_ctx *ctx, const float *phat_dev, int32_t steps, int32_t samples,
+                       int32_t size, uint64_t seed, double out[3]);
+
 /* Advance the context's field (FP32, pitch_x == nx, same stream as the net)
  * by `jumps` learned jumps of guard->steps_per_jump steps each.  Every jump
- * is checked: finite values, energy not above E(phi)(1 + energy_rtol), max
- * |phi_hat| <= max_abs and the residual check; a rejected jump is replaced by
- * that many plain steps (ac_step).  *fallbacks (if non-NULL) receives the
- * number of rejected jumps.  Uses the context's workspace; synchronises once
- * per jump. */
+ * is checked as ac_guard describes (and for non-finite values); a rejected
+ * jump is replaced by that many plain steps (ac_step), so the result is
+ * then bit for bit the plain stepper's.  *fallbacks (if non-NULL) receives
+ * the number of rejected jumps and *report (if non-NULL) the statistics.
+ * Uses the context's workspace for phi_hat and keeps the spot check's
+ * scratch in the network (allocated on first use, kept until
+ * ac_net_destroy); synchronises once per jump. */
 int ac_learned_advance(ac_ctx *ctx, ac_net *net, int64_t jumps, const ac_guard *guard,
-                       int64_t *fallbacks);
+                       int64_t *fallbacks, ac_learned_report *report);
+
+/* Calibration of the guard on held-out jumps of the plain stepper, drawn as
+ * ac_net_train draws its data (cfg: grid n, eps_cells, steps_per_jump,
+ * trajectory_jumps = the age range, pool = the number of held-out states,
+ * seed: use one that training did not):  for each state phi the plain
+ * n-step result P(phi) and the network's jump phi_hat are formed; the
+ * residual threshold is set to residual_factor times the largest residual
+ * max |P(phi) - phi - n dt RHS(phi)| of the plain stepper itself (the
+ * network must be about as consistent as the method it stands for), i.e.
+ * guard->residual_tol is written; the other fields of *guard are kept.
+ * *report (if non-NULL) receives the plain and network residuals and the
+ * network's relative L2 error against P over whole fields next to the spot
+ * check's estimate of it (which uses guard's spot settings).  Allocates its
+ * fields for the duration of the call; synchronises. */
+typedef struct {
+  int32_t states;
+  double plain_residual_max;  /* max over states of the plain jump's residual       */
+  double net_residual_max;    /* the same for the network's jumps                   */
+  double net_rel_err_median;  /* whole-field relative L2 of phi_hat - P(phi)        */
+  double net_rel_err_max;
+  double spot_rel_err_max;    /* the spot check's estimate of the same, max         */
+} ac_guard_calibration;
+int ac_net_calibrate_guard(ac_net *net, const ac_train_config *cfg, double residual_factor,
+                           ac_guard *guard, ac_guard_calibration *report);
 
 /* ------------------------------------------------------ batched mode ---- */
 /* Many independent 2D grids (each its own size, eps, dt and state) advanced
@@ -403,6 +479,59 @@ int ac_batch_launch_count(ac_batch *batch, int64_t *out);
 
 /* Release internal tables (not the caller's buffers).  Synchronises. */
 int ac_batch_destroy(ac_batch *batch);
+
+/* ------------------------------------------------ slab decomposition ---- */
+/* Domain decomposition of one grid along its slowest axis (z in 3D, y in
+ * 2D) into slabs, for grids split over several devices or processes (the
+ * paper's conclusion points at larger simulations; the scheme itself is
+ * Eq. (pytorchACeq) unchanged).  A step of a cell reads its neighbours
+ * only, so n steps of a slab's own planes need the n planes beyond each of
+ * its faces: every part holds `halo` extra planes on each side that faces
+ * another part, advances its extended slab by at most `halo` steps with
+ * the ordinary stepper (the zero-Neumann clamp at an extended slab's
+ * artificial faces corrupts only its halo planes, one plane per step), and
+ * then refreshes its halos from its neighbours' owned planes.  Owned planes
+ * are therefore bit for bit those of the undivided grid (FP16 storage: when
+ * both round at the same pass boundaries; a slab's blocks of `halo` steps
+ * may place them elsewhere, and then the two agree to the storage rounding). */
+typedef struct {
+  int64_t own_lo, own_hi; /* planes this part owns: [own_lo, own_hi)              */
+  int64_t ext_lo, ext_hi; /* planes it holds, owned plus halos: [ext_lo, ext_hi)  */
+} ac_slab_part;
+
+/* Host-only plan, no CUDA call: `extent` planes split into `parts` slabs
+ * of extent / parts planes, the first extent % parts of them one plane
+ * larger; ext_lo = max(0, own_lo - halo), ext_hi = min(extent, own_hi +
+ * halo).  Part p's lower halo [ext_lo, own_lo) is owned by part p - 1 and
+ * its upper halo [own_hi, ext_hi) by part p + 1.  AC_ERR_INVALID unless
+ * 1 <= parts <= extent, halo >= 1 and every part owns >= halo planes (so
+ * each halo comes from one neighbour).  out: parts entries. */
+int ac_slab_plan(int64_t extent, int32_t parts, int32_t halo, ac_slab_part *out);
+
+/* In-process slabs on the current device: `parts` contexts over extended
+ * slabs that this call allocates (field and workspace each; freed by
+ * ac_slab_destroy), all on cuda_stream.  halo = 0 takes twice the default
+ * temporal-block depth of the grid kind and storage type (3D: 4; 2D: 12
+ * for FP32, 8 for FP16 storage; FP64: 2), so that a block is two passes.  Halo exchanges are device-to-device copies of contiguous
+ * plane blocks on the stream. */
+typedef struct ac_slab ac_slab; /* opaque */
+int ac_slab_create(const ac_grid_desc *desc, int32_t parts, int32_t halo, void *cuda_stream,
+                   ac_slab **out);
+/* Copy a whole field (desc's layout, device memory) into the parts, halos
+ * included / the parts' owned planes back into a whole field.  Async. */
+int ac_slab_scatter(ac_slab *slab, const void *phi_dev);
+int ac_slab_gather(ac_slab *slab, void *phi_dev);
+/* n steps: blocks of at most `halo` steps, each part stepped by ac_step,
+ * halos refreshed between blocks.  Async on the stream. */
+int ac_slab_step(ac_slab *slab, int64_t n);
+/* Schedule of every part (as ac_set_schedule). */
+int ac_slab_set_schedule(ac_slab *slab, int32_t variant, int32_t k);
+/* Plan entry, halo depth and field of one part (its layout: desc with the
+ * slow axis extent ext_hi - ext_lo). */
+int ac_slab_get_part(ac_slab *slab, int32_t part, ac_slab_part *plan, int32_t *halo, void **phi_dev);
+/* Kernels and halo copies issued so far (all parts). */
+int ac_slab_launch_count(ac_slab *slab, int64_t *kernels, int64_t *copies);
+int ac_slab_destroy(ac_slab *slab);
 
 /* Allocation-free variant of ac_observe, for callers that cannot allocate
  * device or host memory at the point of the call: code running under a

@@ -6,7 +6,7 @@ handle that allocates device memory.  There is no CPU fallback.
 """
 from ._lib import (AC_ERR_CUDA, AC_ERR_INVALID, AC_ERR_NOMEM, AC_ERR_NONFINITE,  # noqa: F401
                    AC_ERR_TIMEOUT, AC_ERR_UNSUPPORTED, AC_F16S, AC_F32, AC_F64, AC_MAX_K, AC_OK,
-                   AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM, AC_TILE_AUTO, AC_NUM_TILES_3D,
+                   AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM, AC_TILE_AUTO, AC_NUM_TILES_3D, AC_NUM_TILES_2D,
                    AC_SHAPE_DUMBBELL, AC_SHAPE_STAR, AC_SHAPE_TORUS,
                    AcError, AcGridDesc,
                    EXPORTED, ac_autotune, ac_create, ac_destroy, ac_energy, ac_get_schedule,

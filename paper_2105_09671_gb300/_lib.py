@@ -23,7 +23,7 @@ AC_ERR_NOMEM = 6
 AC_F64, AC_F32, AC_F16S = 0, 1, 2
 AC_VARIANT_AUTO, AC_VARIANT_DIRECT, AC_VARIANT_STREAM = 0, 1, 2
 AC_MAX_K = 8
-AC_TILE_AUTO, AC_NUM_TILES_3D = -1, 3
+AC_TILE_AUTO, AC_NUM_TILES_3D, AC_NUM_TILES_2D = -1, 3, 2
 AC_SHAPE_DUMBBELL, AC_SHAPE_STAR, AC_SHAPE_TORUS = 1, 2, 3
 
 EXPORTED = (
@@ -39,7 +39,9 @@ EXPORTED = (
     "ac_net_param_count", "ac_net_create", "ac_net_set_params", "ac_net_get_params",
     "ac_net_forward", "ac_net_loss_grads", "ac_net_adam", "ac_net_train_step",
     "ac_net_launch_count", "ac_net_destroy", "ac_learned_advance", "ac_net_train",
-    "ac_net_init_params", "ac_jump_residual",
+    "ac_net_init_params", "ac_jump_residual", "ac_jump_spot_check", "ac_net_calibrate_guard",
+    "ac_slab_plan", "ac_slab_create", "ac_slab_scatter", "ac_slab_gather", "ac_slab_step",
+    "ac_slab_set_schedule", "ac_slab_get_part", "ac_slab_launch_count", "ac_slab_destroy",
 )
 
 
@@ -63,7 +65,51 @@ class AcGuard(ctypes.Structure):
         ("energy_rtol", ctypes.c_double),
         ("max_abs", ctypes.c_double),
         ("residual_tol", ctypes.c_double),
+        ("spot_rtol", ctypes.c_double),
+        ("spot_samples", ctypes.c_int32),
+        ("spot_size", ctypes.c_int32),
+        ("spot_seed", ctypes.c_uint64),
     ]
+
+
+class AcLearnedReport(ctypes.Structure):
+    _fields_ = [
+        ("jumps", ctypes.c_int64),
+        ("fallbacks", ctypes.c_int64),
+        ("rejected_nonfinite", ctypes.c_int64),
+        ("rejected_energy", ctypes.c_int64),
+        ("rejected_max_abs", ctypes.c_int64),
+        ("rejected_residual", ctypes.c_int64),
+        ("rejected_spot", ctypes.c_int64),
+        ("max_residual", ctypes.c_double),
+        ("max_spot_rel", ctypes.c_double),
+        ("max_spot_abs", ctypes.c_double),
+    ]
+
+
+class AcGuardCalibration(ctypes.Structure):
+    _fields_ = [
+        ("states", ctypes.c_int32),
+        ("plain_residual_max", ctypes.c_double),
+        ("net_residual_max", ctypes.c_double),
+        ("net_rel_err_median", ctypes.c_double),
+        ("net_rel_err_max", ctypes.c_double),
+        ("spot_rel_err_max", ctypes.c_double),
+    ]
+
+
+class AcSlabPart(ctypes.Structure):
+    _fields_ = [
+        ("own_lo", ctypes.c_int64),
+        ("own_hi", ctypes.c_int64),
+        ("ext_lo", ctypes.c_int64),
+        ("ext_hi", ctypes.c_int64),
+    ]
+
+
+def struct_dict(st) -> dict:
+    """The fields of a ctypes structure as a plain dict."""
+    return {name: getattr(st, name) for name, _ in st._fields_}
 
 
 class AcTrainConfig(ctypes.Structure):
@@ -154,7 +200,20 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_net_train_step": [vp, vp, vp, i32, i64, i64, i64, dbl, dbl, ctypes.POINTER(dbl)],
         "ac_net_launch_count": [vp, ctypes.POINTER(i64)],
         "ac_net_destroy": [vp],
-        "ac_learned_advance": [vp, vp, i64, ctypes.POINTER(AcGuard), ctypes.POINTER(i64)],
+        "ac_learned_advance": [vp, vp, i64, ctypes.POINTER(AcGuard), ctypes.POINTER(i64),
+                               ctypes.POINTER(AcLearnedReport)],
+        "ac_jump_spot_check": [vp, vp, i32, i32, i32, u64, ctypes.POINTER(dbl)],
+        "ac_slab_plan": [i64, i32, i32, ctypes.POINTER(AcSlabPart)],
+        "ac_slab_create": [dp, i32, i32, vp, ctypes.POINTER(vp)],
+        "ac_slab_scatter": [vp, vp],
+        "ac_slab_gather": [vp, vp],
+        "ac_slab_step": [vp, i64],
+        "ac_slab_set_schedule": [vp, i32, i32],
+        "ac_slab_get_part": [vp, i32, ctypes.POINTER(AcSlabPart), ctypes.POINTER(i32), ctypes.POINTER(vp)],
+        "ac_slab_launch_count": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "ac_slab_destroy": [vp],
+        "ac_net_calibrate_guard": [vp, ctypes.POINTER(AcTrainConfig), dbl, ctypes.POINTER(AcGuard),
+                                   ctypes.POINTER(AcGuardCalibration)],
         "ac_net_train": [vp, ctypes.POINTER(AcTrainConfig), vp, ctypes.POINTER(i64)],
         "ac_net_init_params": [vp, u64],
         "ac_jump_residual": [vp, vp, i32, ctypes.POINTER(dbl)],
@@ -448,11 +507,31 @@ def ac_net_destroy(net: int) -> None:
     check(lib().ac_net_destroy(ctypes.c_void_p(net)))
 
 
-def ac_learned_advance(ctx: int, net: int, jumps: int, guard: "AcGuard") -> int:
+def ac_learned_advance(ctx: int, net: int, jumps: int, guard: "AcGuard", with_report: bool = False):
+    """Returns the number of rejected jumps, or (that number, the report as
+    a dict) with with_report=True."""
     fb = ctypes.c_int64()
+    rep = AcLearnedReport()
     check(lib().ac_learned_advance(ctypes.c_void_p(ctx), ctypes.c_void_p(net), int(jumps),
-                                   ctypes.byref(guard), ctypes.byref(fb)))
-    return fb.value
+                                   ctypes.byref(guard), ctypes.byref(fb), ctypes.byref(rep)))
+    return (fb.value, struct_dict(rep)) if with_report else fb.value
+
+
+def ac_jump_spot_check(ctx: int, phat_ptr: int, steps: int, samples: int = 0, size: int = 0,
+                       seed: int = 0) -> tuple:
+    """(max |phat - ref|, relative L2 error, cells checked) of the spot check."""
+    out = (ctypes.c_double * 3)()
+    check(lib().ac_jump_spot_check(ctypes.c_void_p(ctx), ctypes.c_void_p(phat_ptr), int(steps),
+                                   int(samples), int(size), int(seed), out))
+    return out[0], out[1], out[2]
+
+
+def ac_net_calibrate_guard(net: int, cfg: "AcTrainConfig", residual_factor: float, guard: "AcGuard") -> dict:
+    """Sets guard.residual_tol in place; returns the calibration report."""
+    rep = AcGuardCalibration()
+    check(lib().ac_net_calibrate_guard(ctypes.c_void_p(net), ctypes.byref(cfg), float(residual_factor),
+                                       ctypes.byref(guard), ctypes.byref(rep)))
+    return struct_dict(rep)
 
 
 def ac_net_train(net: int, cfg: "AcTrainConfig"):
@@ -473,3 +552,53 @@ def ac_jump_residual(ctx: int, phat_ptr: int, steps: int) -> tuple:
     out = (ctypes.c_double * 2)()
     check(lib().ac_jump_residual(ctypes.c_void_p(ctx), ctypes.c_void_p(phat_ptr), int(steps), out))
     return out[0], out[1]
+
+
+def ac_slab_plan(extent: int, parts: int, halo: int) -> list:
+    """[(own_lo, own_hi, ext_lo, ext_hi)] per part (host arithmetic only)."""
+    out = (AcSlabPart * max(1, int(parts)))()
+    check(lib().ac_slab_plan(int(extent), int(parts), int(halo), out))
+    return [(p.own_lo, p.own_hi, p.ext_lo, p.ext_hi) for p in out[:int(parts)]]
+
+
+def ac_slab_create(desc: "AcGridDesc", parts: int, halo: int, stream: int) -> int:
+    out = ctypes.c_void_p()
+    check(lib().ac_slab_create(ctypes.byref(desc), int(parts), int(halo), ctypes.c_void_p(stream),
+                               ctypes.byref(out)))
+    return out.value
+
+
+def ac_slab_scatter(slab: int, phi_ptr: int) -> None:
+    check(lib().ac_slab_scatter(ctypes.c_void_p(slab), ctypes.c_void_p(phi_ptr)))
+
+
+def ac_slab_gather(slab: int, phi_ptr: int) -> None:
+    check(lib().ac_slab_gather(ctypes.c_void_p(slab), ctypes.c_void_p(phi_ptr)))
+
+
+def ac_slab_step(slab: int, n: int) -> None:
+    check(lib().ac_slab_step(ctypes.c_void_p(slab), int(n)))
+
+
+def ac_slab_set_schedule(slab: int, variant: int, k: int) -> None:
+    check(lib().ac_slab_set_schedule(ctypes.c_void_p(slab), int(variant), int(k)))
+
+
+def ac_slab_get_part(slab: int, part: int) -> tuple:
+    """((own_lo, own_hi, ext_lo, ext_hi), halo, device pointer of the part's field)."""
+    pl = AcSlabPart()
+    halo = ctypes.c_int32()
+    ptr = ctypes.c_void_p()
+    check(lib().ac_slab_get_part(ctypes.c_void_p(slab), int(part), ctypes.byref(pl), ctypes.byref(halo),
+                                 ctypes.byref(ptr)))
+    return (pl.own_lo, pl.own_hi, pl.ext_lo, pl.ext_hi), halo.value, ptr.value
+
+
+def ac_slab_launch_count(slab: int) -> tuple:
+    k, c = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ac_slab_launch_count(ctypes.c_void_p(slab), ctypes.byref(k), ctypes.byref(c)))
+    return k.value, c.value
+
+
+def ac_slab_destroy(slab: int) -> None:
+    check(lib().ac_slab_destroy(ctypes.c_void_p(slab)))

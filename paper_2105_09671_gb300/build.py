@@ -22,11 +22,11 @@ LIB = os.path.join(OUT_DIR, "libac.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Kernels use C++20 (templated lambdas for the unrolled streaming loops).
-# ac_batch.cu and ac_net.cu are host-only C++ that needs nothing newer than
+# ac_batch.cu, ac_net.cu and ac_slab.cu are host-only C++ that needs nothing newer than
 # C++17, and nvcc 13.0's front end aborts on them in C++20 mode (an internal
 # assertion when destroying std::vector elements of the C-linkage descriptor
 # types), so they are compiled as C++17.
-STD_OVERRIDE = {"ac_batch.cu": "-std=c++17", "ac_net.cu": "-std=c++17"}
+STD_OVERRIDE = {"ac_batch.cu": "-std=c++17", "ac_net.cu": "-std=c++17", "ac_slab.cu": "-std=c++17"}
 # Sources compiled several times with different defines, one object each
 # (the 3D stencil per tile shape: its kernel instantiations then compile in
 # parallel processes).

@@ -32,6 +32,38 @@ int set_error(int code, const char *msg) {
   g_err = msg;
   return code;
 }
+
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < kSetupDevices;
+  if (cached) {
+    const int v = ks.occ[dev].load(std::memory_order_acquire);
+    if (v > 0) {
+      *occ = v;
+      return cudaSuccess;
+    }
+  }
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cached) {
+    const int v = ks.occ[dev].load(std::memory_order_relaxed);
+    if (v > 0) {
+      *occ = v;
+      return cudaSuccess;
+    }
+  }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int n = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
+  if (e != cudaSuccess) return e;
+  n = n > 1 ? n : 1;
+  if (cached) ks.occ[dev].store(n, std::memory_order_release);
+  *occ = n;
+  return cudaSuccess;
+}
 }  // namespace ac
 
 #define AC_CUDA(call)                                                                    \
@@ -116,7 +148,7 @@ static int encode_map(ac_ctx *c, void *base, int kind, int k, int tile, CUtensor
   cuuint32_t box[3], estr[3] = {1, 1, 1};
   cuuint32_t rank;
   if (kind == 2) {
-    Stream2DGeom gm = stream2d_geom(d.dtype, k);
+    Stream2DGeom gm = stream2d_geom(d.dtype, k, tile);
     box[0] = gm.box_x; box[1] = gm.box_y; box[2] = 1;
     rank = 2;
   } else {
@@ -215,24 +247,27 @@ extern "C" int ac_destroy(ac_ctx *c) {
 static bool schedule_ok(const ac_ctx *c, int variant, int k, int tile = 0) {
   if (variant == AC_VARIANT_DIRECT) return k == 1;
   if (variant == AC_VARIANT_STREAM)
-    return c->d.ndim == 2 ? tile == 0 && stream2d_supported(c->d.dtype, k)
+    return c->d.ndim == 2 ? stream2d_supported(c->d.dtype, k, tile)
                           : stream3d_supported(c->d.dtype, k, tile);
   return false;
 }
 
-static void default_schedule(const ac_ctx *c, int *variant, int *k) {
+int ac_default_depth(int ndim, int dtype) {
   // FP64 is bound by the GPU's FP64 rate, where the redundant halo work of
   // temporal blocking costs more than the memory traffic it saves: one step
-  // per launch.  FP32 / FP16 storage are memory bound: stream with k > 1
-  // (measured best on GB300: 3D k = 2, 2D k = 4).
-  if (c->d.dtype == AC_F64) {
-    *variant = AC_VARIANT_DIRECT;
+  // per launch.  FP32 / FP16 storage stream with k > 1 (measured best on
+  // GB300: 3D k = 2; 2D FP32 k = 6 with 8-cell strips, FP16 storage k = 4).
+  if (dtype == AC_F64) return 1;
+  if (ndim == 3) return 2;
+  return dtype == AC_F32 ? 6 : 4;
+}
+
+static void default_schedule(const ac_ctx *c, int *variant, int *k) {
+  *variant = c->d.dtype == AC_F64 ? AC_VARIANT_DIRECT : AC_VARIANT_STREAM;
+  *k = ac_default_depth(c->d.ndim, c->d.dtype);
+  if (*variant == AC_VARIANT_STREAM && !schedule_ok(c, *variant, *k, 0) &&
+      !schedule_ok(c, *variant, *k, 1))
     *k = 1;
-    return;
-  }
-  *variant = AC_VARIANT_STREAM;
-  *k = c->d.ndim == 2 ? 4 : 2;
-  if (!schedule_ok(c, *variant, *k)) *k = 1;
 }
 
 static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
@@ -246,6 +281,10 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
 // k <= 2 (FP16 storage at k = 1: several CTAs per SM, tile 1); k = 3 needs
 // the register room of four rows per thread with half the threads (tile 2).
 static int default_tile(const ac_ctx *c, int k) {
+  // 2D FP32: strips of 8 cells per lane wherever they are offered (k <= 6;
+  // 4096^2 at k = 6: 1634 against 1485 Gcell-updates/s for 4-cell strips at
+  // k = 4, 8192^2: 2006 against 1841)
+  if (c->d.ndim == 2) return c->d.dtype == AC_F32 && k <= 6 ? 1 : 0;
   if (c->d.dtype == AC_F64) return k == 1 ? 0 : 2;
   if (c->d.dtype == AC_F16S) return k == 1 ? 1 : 0;
   return k == 3 ? 2 : 0;
@@ -254,7 +293,7 @@ static int default_tile(const ac_ctx *c, int k) {
 // The tile of a streaming launch: the user's, else the autotuner's (when it
 // is available at this depth), else the default.
 static int effective_tile(const ac_ctx *c, int variant, int k) {
-  if (variant != AC_VARIANT_STREAM || c->d.ndim != 3) return 0;
+  if (variant != AC_VARIANT_STREAM) return 0;
   if (c->tile != AC_TILE_AUTO && schedule_ok(c, variant, k, c->tile)) return c->tile;
   if (c->tuned_variant && schedule_ok(c, variant, k, c->tuned_tile)) return c->tuned_tile;
   const int t = default_tile(c, k);
@@ -282,8 +321,10 @@ extern "C" int ac_set_schedule(ac_ctx *c, int32_t variant, int32_t k) {
 extern "C" int ac_set_tile(ac_ctx *c, int32_t tile) {
   if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
   if (tile == AC_TILE_AUTO) { c->tile = AC_TILE_AUTO; return AC_OK; }
-  if (tile < 0 || tile >= AC_NUM_TILES_3D) return fail(AC_ERR_INVALID, "tile must be in 0..%d", AC_NUM_TILES_3D - 1);
-  if (c->d.ndim == 2 && tile != 0) return fail(AC_ERR_UNSUPPORTED, "2D grids have tile 0 only");
+  const int ntiles = c->d.ndim == 3 ? AC_NUM_TILES_3D : AC_NUM_TILES_2D;
+  if (tile < 0 || tile >= ntiles) return fail(AC_ERR_INVALID, "tile must be in 0..%d", ntiles - 1);
+  if (c->d.ndim == 2 && tile != 0 && !stream2d_supported(c->d.dtype, 1, tile))
+    return fail(AC_ERR_UNSUPPORTED, "2D tile %d is offered for FP32 storage only", tile);
   c->tile = tile;
   return AC_OK;
 }
@@ -343,7 +384,7 @@ static int issue_steps(ac_ctx *c, int64_t n, int variant, int k, int tile) {
       int rc = ensure_maps(c, dep, tl);
       if (rc) return rc;
       const CUtensorMap *m = src_is_phi ? &c->maps[tl][dep].phi : &c->maps[tl][dep].ws;
-      e = c->d.ndim == 2 ? launch_stream2d(c->d.dtype, dep, c->gp, m, dst, c->num_sms, c->stream)
+      e = c->d.ndim == 2 ? launch_stream2d(c->d.dtype, dep, tl, c->gp, m, dst, c->num_sms, c->stream)
                          : launch_stream3d(c->d.dtype, dep, tl, c->gp, m, dst, c->num_sms, c->stream);
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stencil launch failed: %s", cudaGetErrorString(e));
@@ -574,7 +615,7 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   std::vector<TuneChoice> cand;
   cand.push_back({AC_VARIANT_DIRECT, 1, 0});
   for (int k = 1; k <= AC_MAX_K; ++k)
-    for (int tile = 0; tile < (c->d.ndim == 3 ? AC_NUM_TILES_3D : 1); ++tile)
+    for (int tile = 0; tile < (c->d.ndim == 3 ? AC_NUM_TILES_3D : AC_NUM_TILES_2D); ++tile)
       if (schedule_ok(c, AC_VARIANT_STREAM, k, tile)) cand.push_back({AC_VARIANT_STREAM, k, tile});
   const size_t bytes = field_bytes(&c->d);
   void *backup = nullptr;
@@ -672,9 +713,22 @@ extern "C" int ac_tc_gemm_bf16_n32(const void *a_dev, const void *b_dev, float *
     return fail(AC_ERR_INVALID, "need m a multiple of 128 and k a multiple of 16 in [16, 512]");
   if (((uintptr_t)a_dev | (uintptr_t)b_dev | (uintptr_t)d_dev) & 15)
     return fail(AC_ERR_INVALID, "operands must be 16-byte aligned");
-  static int *status = nullptr;
-  if (!status && cudaMalloc(&status, sizeof(int)) != cudaSuccess)
-    return fail(AC_ERR_NOMEM, "status word allocation failed");
+  // one status word per device, allocated on the device's first call
+  static std::mutex mu;
+  static int *status_of[kSetupDevices] = {nullptr};
+  int dev = 0;
+  AC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kSetupDevices) return fail(AC_ERR_UNSUPPORTED, "device index %d too large", dev);
+  int *status = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!status_of[dev] && cudaMalloc(&status_of[dev], sizeof(int)) != cudaSuccess) {
+      status_of[dev] = nullptr;
+      cudaGetLastError();
+      return fail(AC_ERR_NOMEM, "status word allocation failed");
+    }
+    status = status_of[dev];
+  }
   cudaError_t e = launch_tc_gemm_n32(a_dev, b_dev, d_dev, m, k, status, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return fail(AC_ERR_CUDA, "tensor-core GEMM launch failed: %s", cudaGetErrorString(e));
   return AC_OK;

@@ -45,8 +45,45 @@ struct ac_net {
   int adam_step = 0;
   bool grads_valid = false;
   unsigned int *guard = nullptr;  // 2 words: guard maxima
+  // spot check of the guard: box scratch, per-box partials, result, and a
+  // pinned host copy of one jump's guard quantities
+  float *spot_scratch = nullptr;
+  size_t spot_floats = 0;
+  double *spot_partials = nullptr;
+  int spot_cap = 0;
+  double *spot_out = nullptr;  // 4 doubles
+  double *h_res = nullptr;     // pinned: [0..1] guard words, [2..5] observe, [6..9] spot
   int64_t launches = 0;
 };
+
+static int ensure_spot(ac_net *net, size_t floats, int samples) {
+  if (net->spot_floats < floats) {
+    cudaFree(net->spot_scratch);
+    net->spot_scratch = nullptr;
+    net->spot_floats = 0;
+    NC_CUDA(cudaMalloc(&net->spot_scratch, floats * sizeof(float)));
+    net->spot_floats = floats;
+  }
+  if (net->spot_cap < samples) {
+    cudaFree(net->spot_partials);
+    net->spot_partials = nullptr;
+    net->spot_cap = 0;
+    NC_CUDA(cudaMalloc(&net->spot_partials, (size_t)samples * 4 * sizeof(double)));
+    net->spot_cap = samples;
+  }
+  return AC_OK;
+}
+
+static void spot_settings(int ndim, const ac_guard *g, int *samples, int *size) {
+  *samples = g->spot_samples > 0 ? g->spot_samples : (ndim == 3 ? 16 : 64);
+  *size = g->spot_size > 0 ? g->spot_size : (ndim == 3 ? 8 : 32);
+}
+
+static double rel_from(double d2, double r2) {
+  if (!(d2 == d2)) return INFINITY;
+  if (r2 > 0) return std::sqrt(d2 / r2);
+  return d2 > 0 ? INFINITY : 0.0;
+}
 
 static void free_shape(ShapeBufs &s) {
   for (int i = 0; i < 5; ++i) {
@@ -170,6 +207,8 @@ extern "C" int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out) {
   if (e == cudaSuccess) e = cudaMalloc(&b.loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&net->guard, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&net->spot_out, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&net->h_res, 10 * sizeof(double));
   std::vector<float> init;
   he_init(b.layout, 0, init);
   if (e == cudaSuccess) e = cudaMemcpy(b.params, init.data(), pbytes, cudaMemcpyHostToDevice);
@@ -181,6 +220,7 @@ extern "C" int ac_net_create(int32_t ndim, void *cuda_stream, ac_net **out) {
   if (e != cudaSuccess) {
     cudaFree(b.params); cudaFree(b.grads); cudaFree(b.m); cudaFree(b.v);
     cudaFree(b.wf); cudaFree(b.wd); cudaFree(b.loss); cudaFree(b.status); cudaFree(net->guard);
+    cudaFree(net->spot_out); cudaFreeHost(net->h_res);
     delete net;
     cudaGetLastError();
     return nfail(AC_ERR_NOMEM, "network allocation failed: %s", cudaGetErrorString(e));
@@ -197,6 +237,8 @@ extern "C" int ac_net_destroy(ac_net *net) {
   NetBuffers &b = net->base;
   cudaFree(b.params); cudaFree(b.grads); cudaFree(b.m); cudaFree(b.v);
   cudaFree(b.wf); cudaFree(b.wd); cudaFree(b.loss); cudaFree(b.status); cudaFree(net->guard);
+  cudaFree(net->spot_out); cudaFreeHost(net->h_res);
+  cudaFree(net->spot_scratch); cudaFree(net->spot_partials);
   delete net;
   return AC_OK;
 }
@@ -330,48 +372,114 @@ extern "C" int ac_jump_residual(ac_ctx *c, const float *phat_dev, int32_t steps,
   return AC_OK;
 }
 
+extern "C" int ac_jump_spot_check(ac_ctx *c, const float *phat_dev, int32_t steps, int32_t samples,
+                                  int32_t size, uint64_t seed, double out[3]) {
+  if (!c || !phat_dev || !out) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (c->d.dtype != AC_F32) return nfail(AC_ERR_UNSUPPORTED, "needs an FP32 context");
+  if (steps < 1 || samples < 0 || size < 0) return nfail(AC_ERR_INVALID, "steps >= 1, samples and size >= 0");
+  ac_guard gd{};
+  gd.spot_samples = samples;
+  gd.spot_size = size;
+  int ns, sz;
+  spot_settings(c->d.ndim, &gd, &ns, &sz);
+  const size_t floats = spot_scratch_floats(c->gp, c->d.ndim, steps, ns, sz);
+  float *scratch = nullptr;
+  double *part = nullptr, *dout = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, floats * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)ns * 4 * sizeof(double) + 4 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(scratch);
+    cudaGetLastError();
+    return nfail(AC_ERR_NOMEM, "spot-check scratch allocation failed");
+  }
+  dout = part + (size_t)ns * 4;
+  e = launch_spot_check(static_cast<const float *>(c->phi), phat_dev, c->gp, c->d.ndim, steps, ns, sz,
+                        seed, scratch, part, dout, c->stream);
+  double h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  cudaFree(part);
+  if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "spot check failed: %s", cudaGetErrorString(e));
+  c->launches += 2;
+  out[0] = h[0];
+  out[1] = rel_from(h[1], h[2]);
+  out[2] = h[3];
+  return AC_OK;
+}
+
 extern "C" int ac_learned_advance(ac_ctx *c, ac_net *net, int64_t jumps, const ac_guard *guard,
-                                  int64_t *fallbacks) {
+                                  int64_t *fallbacks, ac_learned_report *report) {
   if (!c || !net || !guard) return nfail(AC_ERR_INVALID, "NULL argument");
   if (jumps < 0) return nfail(AC_ERR_INVALID, "jumps must be >= 0");
   if (c->d.dtype != AC_F32) return nfail(AC_ERR_UNSUPPORTED, "the learned stepper runs on FP32 fields");
   if (c->d.ndim != net->ndim) return nfail(AC_ERR_INVALID, "network and grid dimensions differ");
   if (c->d.pitch_x != c->d.nx) return nfail(AC_ERR_UNSUPPORTED, "the learned stepper needs pitch_x == nx");
   if (guard->steps_per_jump < 1) return nfail(AC_ERR_INVALID, "steps_per_jump must be >= 1");
+  if (guard->spot_samples < 0 || guard->spot_size < 0)
+    return nfail(AC_ERR_INVALID, "spot_samples and spot_size must be >= 0");
   if (c->stream != net->stream) return nfail(AC_ERR_INVALID, "context and network must share a stream");
   const int n = guard->steps_per_jump;
   const double scale = n * c->gp.alpha;  // s = n dt / eps^2
   float *phi = static_cast<float *>(c->phi);
   float *phat = static_cast<float *>(c->ws);
-  unsigned int *gbuf = net->guard;
+  const bool use_spot = guard->spot_rtol > 0;
+  int ns = 0, sz = 0;
+  spot_settings(c->d.ndim, guard, &ns, &sz);
+  if (use_spot) {
+    const int rc = ensure_spot(net, spot_scratch_floats(c->gp, c->d.ndim, n, ns, sz), ns);
+    if (rc) return rc;
+  }
+  ac_learned_report rep{};
   int64_t fb = 0;
-  double e_cur = 0.0, obs[3];
+  double obs[3];
   int rc = ac_observe(c, obs);
   if (rc) return rc;
-  e_cur = obs[0];
+  double e_cur = obs[0];
+  const double hd = c->d.ndim == 3 ? c->d.h * c->d.h * c->d.h : c->d.h * c->d.h;
+  double *hr = net->h_res;
   for (int64_t j = 0; j < jumps; ++j) {
     rc = ac_net_forward(net, phi, phat, 1, c->d.nx, c->d.ny, c->d.nz, scale);
     if (rc) return rc;
-    cudaError_t e = launch_guard(phi, phat, c->gp, c->d.ndim, n, gbuf, c->stream);
+    cudaError_t e = launch_guard(phi, phat, c->gp, c->d.ndim, n, net->guard, c->stream);
+    if (e == cudaSuccess)  // energy of phi_hat (FP64 reduction over the workspace)
+      e = launch_observe(c->d.dtype, c->gp, phat, c->d_partials, c->d_out, c->stream);
+    if (e == cudaSuccess && use_spot)
+      e = launch_spot_check(phi, phat, c->gp, c->d.ndim, n, ns, sz, guard->spot_seed + (uint64_t)j,
+                            net->spot_scratch, net->spot_partials, net->spot_out, c->stream);
     if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "guard launch failed: %s", cudaGetErrorString(e));
-    unsigned int gh[2];
-    NC_CUDA(cudaMemcpyAsync(gh, gbuf, sizeof gh, cudaMemcpyDeviceToHost, c->stream));
-    // energy of phi_hat (FP64 reduction over the workspace)
-    e = launch_observe(c->d.dtype, c->gp, phat, c->d_partials, c->d_out, c->stream);
-    if (e != cudaSuccess) return nfail(AC_ERR_CUDA, "reduction launch failed: %s", cudaGetErrorString(e));
-    NC_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NC_CUDA(cudaMemcpyAsync(hr, net->guard, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    NC_CUDA(cudaMemcpyAsync(hr + 2, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (use_spot)
+      NC_CUDA(cudaMemcpyAsync(hr + 6, net->spot_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NC_CUDA(cudaStreamSynchronize(c->stream));
-    c->launches += 3;
+    c->launches += 3 + (use_spot ? 2 : 0);
+    unsigned int gw[2];
+    memcpy(gw, hr, sizeof gw);
     float mabs, mres;
-    memcpy(&mabs, &gh[0], 4);
-    memcpy(&mres, &gh[1], 4);
-    const double hd = c->d.ndim == 3 ? c->d.h * c->d.h * c->d.h : c->d.h * c->d.h;
-    const double e_new = hd * (c->h_out[0] / (c->d.eps * c->d.eps) + 0.5 * c->h_out[1] / (c->d.h * c->d.h));
-    const bool finite = c->h_out[3] == 0.0 && std::isfinite(e_new);
-    const bool ok = finite && e_new <= e_cur * (1.0 + guard->energy_rtol) + 1e-300 &&
-                    mabs <= guard->max_abs &&
-                    (guard->residual_tol <= 0 || mres <= guard->residual_tol);
-    if (ok) {
+    memcpy(&mabs, &gw[0], 4);
+    memcpy(&mres, &gw[1], 4);
+    const double e_new = hd * (hr[2] / (c->d.eps * c->d.eps) + 0.5 * hr[3] / (c->d.h * c->d.h));
+    const bool finite = hr[5] == 0.0 && std::isfinite(e_new) && std::isfinite(mres);
+    const bool ok_e = e_new <= e_cur * (1.0 + guard->energy_rtol) + 1e-300;
+    const bool ok_m = mabs <= guard->max_abs;
+    const bool ok_r = guard->residual_tol <= 0 || mres <= guard->residual_tol;
+    double spot_rel = 0.0, spot_abs = 0.0;
+    if (use_spot) {
+      spot_abs = hr[6];
+      spot_rel = rel_from(hr[7], hr[8]);
+    }
+    const bool ok_s = !use_spot || spot_rel <= guard->spot_rtol;
+    ++rep.jumps;
+    rep.rejected_nonfinite += !finite;
+    rep.rejected_energy += !ok_e;
+    rep.rejected_max_abs += !ok_m;
+    rep.rejected_residual += !ok_r;
+    rep.rejected_spot += !ok_s;
+    rep.max_residual = std::max(rep.max_residual, (double)mres);
+    rep.max_spot_rel = std::max(rep.max_spot_rel, spot_rel);
+    rep.max_spot_abs = std::max(rep.max_spot_abs, spot_abs);
+    if (finite && ok_e && ok_m && ok_r && ok_s) {
       const size_t bytes = (size_t)c->d.nx * c->d.ny * c->d.nz * sizeof(float);
       NC_CUDA(cudaMemcpyAsync(phi, phat, bytes, cudaMemcpyDeviceToDevice, c->stream));
       e_cur = e_new;
@@ -384,7 +492,9 @@ extern "C" int ac_learned_advance(ac_ctx *c, ac_net *net, int64_t jumps, const a
       e_cur = obs[0];
     }
   }
+  rep.fallbacks = fb;
   if (fallbacks) *fallbacks = fb;
+  if (report) *report = rep;
   return AC_OK;
 }
 
@@ -404,17 +514,35 @@ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
+
+// Initial state number `index` of the data recipe under `seed`: even
+// indices a random state of amplitude 0.1, odd ones a tanh circle / sphere
+// of radius uniform in [0.1, 0.4] centred in the unit domain (Section 3.1).
+cudaError_t draw_state(const GridParams &g, float *dst, uint64_t seed, int64_t index, double h,
+                       double eps, cudaStream_t s) {
+  const uint64_t r = mix64(seed * 0x100000001B3ull + (uint64_t)index);
+  if (index % 2 == 0) return launch_init_random(AC_F32, g, dst, r, 0.1, s);
+  const double r0 = 0.1 + 0.3 * (double)(r >> 11) * 0x1.0p-53;
+  const double lo[3] = {0, 0, 0}, c3[3] = {0.5, 0.5, 0.5};
+  return launch_init_sphere(AC_F32, g, dst, h, lo, c3, r0, eps, s);
+}
+
+int check_train_config(const ac_train_config *cfg) {
+  const int n = cfg->n, B = cfg->pool, spj = cfg->steps_per_jump;
+  if (n < 8 || n > 4096 || n % 4) return nfail(AC_ERR_INVALID, "n must be a multiple of 4 in [8, 4096]");
+  if (B < 1 || B > 4096 || cfg->iterations < 1 || spj < 1 || cfg->trajectory_jumps < 1)
+    return nfail(AC_ERR_INVALID, "pool, iterations, steps_per_jump, trajectory_jumps must be >= 1");
+  if (!(cfg->eps_cells > 0) || !(cfg->lr > 0) || !(cfg->lr_final >= 0))
+    return nfail(AC_ERR_INVALID, "eps_cells and lr must be > 0");
+  return AC_OK;
+}
 }  // namespace
 
 extern "C" int ac_net_train(ac_net *net, const ac_train_config *cfg, double *loss_history,
                             int64_t *trajectories_used) {
   if (!net || !cfg) return nfail(AC_ERR_INVALID, "NULL argument");
   const int nd = net->ndim, n = cfg->n, B = cfg->pool, spj = cfg->steps_per_jump;
-  if (n < 8 || n > 4096 || n % 4) return nfail(AC_ERR_INVALID, "n must be a multiple of 4 in [8, 4096]");
-  if (B < 1 || B > 4096 || cfg->iterations < 1 || spj < 1 || cfg->trajectory_jumps < 1)
-    return nfail(AC_ERR_INVALID, "pool, iterations, steps_per_jump, trajectory_jumps must be >= 1");
-  if (!(cfg->eps_cells > 0) || !(cfg->lr > 0) || !(cfg->lr_final >= 0))
-    return nfail(AC_ERR_INVALID, "eps_cells and lr must be > 0");
+  if (int rc0 = check_train_config(cfg)) return rc0;
   const int64_t cells = nd == 3 ? (int64_t)n * n * n : (int64_t)n * n;
   const double h = 1.0 / n, eps = cfg->eps_cells * h, dt = 0.1 * h * h;
   const double scale = spj * dt / (eps * eps);
@@ -468,15 +596,7 @@ extern "C" int ac_net_train(ac_net *net, const ac_train_config *cfg, double *los
   int64_t used = 0;
   auto new_trajectory = [&](int slot) -> int {
     float *dst = states + (size_t)slot * cells;
-    const uint64_t r = mix64(cfg->seed * 0x100000001B3ull + (uint64_t)used);
-    cudaError_t e;
-    if (used % 2 == 0) {
-      e = launch_init_random(AC_F32, g, dst, r, 0.1, s);
-    } else {
-      const double r0 = 0.1 + 0.3 * (double)(r >> 11) * 0x1.0p-53;
-      const double lo[3] = {0, 0, 0}, c3[3] = {0.5, 0.5, 0.5};
-      e = launch_init_sphere(AC_F32, g, dst, h, lo, c3, r0, eps, s);
-    }
+    const cudaError_t e = draw_state(g, dst, cfg->seed, used, h, eps, s);
     ++used;
     ++net->launches;
     return e == cudaSuccess ? AC_OK : nfail(AC_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(e));
@@ -539,4 +659,104 @@ extern "C" int ac_net_train(ac_net *net, const ac_train_config *cfg, double *los
   if (trajectories_used) *trajectories_used = used;
   cleanup();
   return rc;
+}
+
+// ------------------------------------------------------------- calibration --
+extern "C" int ac_net_calibrate_guard(ac_net *net, const ac_train_config *cfg, double residual_factor,
+                                      ac_guard *guard, ac_guard_calibration *report) {
+  if (!net || !cfg || !guard) return nfail(AC_ERR_INVALID, "NULL argument");
+  if (int rc0 = check_train_config(cfg)) return rc0;
+  if (!(residual_factor > 0)) return nfail(AC_ERR_INVALID, "residual_factor must be > 0");
+  if (guard->spot_samples < 0 || guard->spot_size < 0)
+    return nfail(AC_ERR_INVALID, "spot_samples and spot_size must be >= 0");
+  const int nd = net->ndim, n = cfg->n, states = cfg->pool, spj = cfg->steps_per_jump;
+  const int64_t cells = nd == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const double h = 1.0 / n, eps = cfg->eps_cells * h, dt = 0.1 * h * h;
+  const double scale = spj * dt / (eps * eps);
+  cudaStream_t s = net->stream;
+  const size_t fbytes = (size_t)cells * sizeof(float);
+  float *phi = nullptr, *tgt = nullptr, *ws = nullptr, *phat = nullptr;
+  ac_ctx *cphi = nullptr, *ctgt = nullptr;
+  auto cleanup = [&]() {
+    if (cphi) ac_destroy(cphi);
+    if (ctgt) ac_destroy(ctgt);
+    cudaFree(phi);
+    cudaFree(tgt);
+    cudaFree(ws);
+    cudaFree(phat);
+  };
+  if (cudaMalloc(&phi, fbytes) != cudaSuccess || cudaMalloc(&tgt, fbytes) != cudaSuccess ||
+      cudaMalloc(&ws, fbytes) != cudaSuccess || cudaMalloc(&phat, fbytes) != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return nfail(AC_ERR_NOMEM, "calibration fields do not fit");
+  }
+  ac_grid_desc d{};
+  d.ndim = nd;
+  d.dtype = AC_F32;
+  d.nx = n;
+  d.ny = n;
+  d.nz = nd == 3 ? n : 1;
+  d.pitch_x = n;
+  d.h = h;
+  d.eps = eps;
+  d.dt = dt;
+  int rc = ac_create(&d, phi, ws, s, &cphi);
+  if (rc == AC_OK) rc = ac_create(&d, tgt, ws, s, &ctgt);
+  int ns = 0, sz = 0;
+  spot_settings(nd, guard, &ns, &sz);
+  if (rc == AC_OK) rc = ensure_spot(net, spot_scratch_floats(cphi->gp, nd, spj, ns, sz), ns);
+  if (rc) { cleanup(); return rc; }
+  GridParams g = cphi->gp;
+  double plain_max = 0.0, net_max = 0.0, spot_max = 0.0;
+  std::vector<double> rel;
+  for (int i = 0; i < states && rc == AC_OK; ++i) {
+    // a held-out state: drawn as the training data are, at a staggered age
+    cudaError_t e = draw_state(g, phi, cfg->seed, i, h, eps, s);
+    if (e != cudaSuccess) { rc = nfail(AC_ERR_CUDA, "init failed: %s", cudaGetErrorString(e)); break; }
+    const int64_t age = (int64_t)i * cfg->trajectory_jumps / states;
+    rc = ac_step(cphi, age * spj);
+    if (rc) break;
+    // the plain stepper's jump P(phi) and its residual
+    if (cudaMemcpyAsync(tgt, phi, fbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      rc = nfail(AC_ERR_CUDA, "copy failed");
+      break;
+    }
+    rc = ac_step(ctgt, spj);
+    double r2[2];
+    if (rc == AC_OK) rc = ac_jump_residual(cphi, tgt, spj, r2);
+    if (rc) break;
+    plain_max = std::max(plain_max, r2[1]);
+    // the network's jump: its residual, its error against P over the whole
+    // field and the spot check's estimate of that error
+    rc = ac_net_forward(net, phi, phat, 1, n, n, d.nz, scale);
+    if (rc == AC_OK) rc = ac_jump_residual(cphi, phat, spj, r2);
+    if (rc) break;
+    net_max = std::max(net_max, r2[1]);
+    double *hr = net->h_res;
+    e = launch_diff_norms(phat, tgt, cells, cphi->d_partials, cphi->d_out, s);
+    if (e == cudaSuccess)
+      e = launch_spot_check(phi, phat, g, nd, spj, ns, sz, guard->spot_seed + (uint64_t)i, net->spot_scratch,
+                            net->spot_partials, net->spot_out, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr + 2, cphi->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr + 6, net->spot_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rc = nfail(AC_ERR_CUDA, "calibration reduction failed: %s", cudaGetErrorString(e)); break; }
+    net->launches += 4;
+    rel.push_back(rel_from(hr[3], hr[4]));
+    spot_max = std::max(spot_max, rel_from(hr[7], hr[8]));
+  }
+  cleanup();
+  if (rc) return rc;
+  std::sort(rel.begin(), rel.end());
+  guard->residual_tol = residual_factor * plain_max;
+  if (report) {
+    report->states = states;
+    report->plain_residual_max = plain_max;
+    report->net_residual_max = net_max;
+    report->net_rel_err_median = rel.empty() ? 0.0 : rel[rel.size() / 2];
+    report->net_rel_err_max = rel.empty() ? 0.0 : rel.back();
+    report->spot_rel_err_max = spot_max;
+  }
+  return AC_OK;
 }

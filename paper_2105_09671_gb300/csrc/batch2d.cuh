@@ -141,23 +141,12 @@ cudaError_t batch2d_launch_t(const BInst *insts, const BItem *items, int n_items
                              const CUtensorMap *maps, int *progress,
                              unsigned long long *ticket, long long total, int *status,
                              uint32_t wait_limit, int num_sms, cudaStream_t s, int *grid_out) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static unsigned attr_mask = 0;
-  static int occ_cache[32] = {0};
-  if (dev < 32 && !(attr_mask & (1u << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(batch2d_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         BatchGeom<T>::SMEM);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch2d_k<T>, kS2Warps * 32,
-                                                      BatchGeom<T>::SMEM);
-    if (e != cudaSuccess) return e;
-    occ_cache[dev] = std::max(1, occ);
-    attr_mask |= 1u << dev;
-  }
+  static KernelSetup ks;
+  int occ = 1;
+  cudaError_t e = kernel_setup(ks, (const void *)batch2d_k<T>, kS2Warps * 32, BatchGeom<T>::SMEM, &occ);
+  if (e != cudaSuccess) return e;
   // every CTA of the grid must be resident at once (the waits rely on it)
-  const int blocks = std::max(1, num_sms) * (dev < 32 ? occ_cache[dev] : 1);
+  const int blocks = std::max(1, num_sms) * occ;
   if (grid_out) *grid_out = blocks;
   batch2d_k<T><<<blocks, kS2Warps * 32, BatchGeom<T>::SMEM, s>>>(
       insts, items, n_items, maps, progress, ticket, total, status, wait_limit);

@@ -49,6 +49,26 @@ __device__ __forceinline__ uint4 pack16(const typename Traits<T>::C *in) {
   for (int i = 0; i < V; ++i) e[i] = from_c<T>(in[i]);
   return w;
 }
+// FP16 storage: convert in pairs (one conversion instruction per two
+// values each way; rounding to nearest even as the scalar form).
+template <>
+__device__ __forceinline__ void unpack16<__half>(const uint4 &w, float *out) {
+  const __half2 *p = reinterpret_cast<const __half2 *>(&w);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(p[i]);
+    out[2 * i] = f.x;
+    out[2 * i + 1] = f.y;
+  }
+}
+template <>
+__device__ __forceinline__ uint4 pack16<__half>(const float *in) {
+  uint4 w;
+  __half2 *p = reinterpret_cast<__half2 *>(&w);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = __floats2half2_rn(in[2 * i], in[2 * i + 1]);
+  return w;
+}
 
 // ------------------------------------------------------------ the update --
 // One explicit Euler step of Eq. (pytorchACeq) for one cell:

@@ -5,7 +5,7 @@ namespace ac {
 
 cudaError_t stream2d_launch_f64(int k, const GridParams &g, const CUtensorMap *map, void *dst,
                               int num_sms, cudaStream_t s) {
-  return s2_dispatch<double>(k, g, map, dst, num_sms, s);
+  return s2_dispatch<double, S2Cfg<double>::VPL>(k, g, map, dst, num_sms, s);
 }
 
 }  // namespace ac

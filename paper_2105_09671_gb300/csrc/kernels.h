@@ -1,6 +1,9 @@
 // Host-side launchers of the CUDA kernels (called by the C-ABI layer).
 #pragma once
 
+#include <algorithm>
+#include <atomic>
+
 #include "common.cuh"
 
 namespace ac {
@@ -20,8 +23,10 @@ struct Stream3DGeom {
   int smem_bytes;
 };
 
-bool stream2d_supported(int dtype, int k);
-Stream2DGeom stream2d_geom(int dtype, int k);
+// 2D strip widths ("tiles"): 0 = the storage type's default (FP32: 4 cells
+// per lane), 1 = 8 FP32 cells per lane (FP32 only).
+bool stream2d_supported(int dtype, int k, int tile);
+Stream2DGeom stream2d_geom(int dtype, int k, int tile);
 bool stream3d_supported(int dtype, int k, int tile);
 Stream3DGeom stream3d_geom(int dtype, int k, int tile);
 
@@ -30,7 +35,7 @@ cudaError_t launch_direct(int ndim, int dtype, const GridParams &g, const void *
                           cudaStream_t s);
 // k steps per launch.  src_map describes the source field with the box of
 // stream{2,3}d_geom(dtype, k).
-cudaError_t launch_stream2d(int dtype, int k, const GridParams &g, const CUtensorMap *src_map,
+cudaError_t launch_stream2d(int dtype, int k, int tile, const GridParams &g, const CUtensorMap *src_map,
                             void *dst, int num_sms, cudaStream_t s);
 cudaError_t launch_stream3d(int dtype, int k, int tile, const GridParams &g,
                             const CUtensorMap *src_map, void *dst, int num_sms, cudaStream_t s);
@@ -54,6 +59,23 @@ cudaError_t launch_observe_noalloc(int dtype, const GridParams &g, const void *p
 cudaError_t launch_guard(const float *phi, const float *phat, const GridParams &g, int ndim,
                          int nsteps, unsigned int *out_dev, cudaStream_t s);
 
+// Spot check of a learned jump (FP32 fields, pitch == nx): the plain
+// stepper's nsteps-step result from phi, computed exactly on `samples` boxes
+// of side size + 2 nsteps (clipped to the grid) placed by `seed`, compared
+// with phat on the exact cells.  scratch: spot_scratch_floats() floats;
+// partials: 4 * samples doubles; out[4] = {max |phat - ref|, sum (phat -
+// ref)^2, sum ref^2, cells compared} (device memory).
+void spot_box(const GridParams &g, int ndim, int nsteps, int size, int box[3]);
+size_t spot_scratch_floats(const GridParams &g, int ndim, int nsteps, int samples, int size);
+cudaError_t launch_spot_check(const float *phi, const float *phat, const GridParams &g, int ndim,
+                              int nsteps, int samples, int size, uint64_t seed, float *scratch,
+                              double *partials, double *out, cudaStream_t s);
+// out[4] = {max |a - b|, sum (a - b)^2, sum b^2, n} over n contiguous floats;
+// partials: 4 * diff_norms_blocks() doubles.
+int diff_norms_blocks();
+cudaError_t launch_diff_norms(const float *a, const float *b, int64_t n, double *partials,
+                              double *out, cudaStream_t s);
+
 cudaError_t launch_init_sphere(int dtype, const GridParams &g, void *phi, double h,
                                const double lower[3], const double center[3], double r0,
                                double eps, cudaStream_t s);
@@ -71,6 +93,20 @@ cudaError_t launch_tc_gemm_n32(const void *a, const void *b, float *d, int64_t m
 // ---- helpers shared by the C-ABI translation units (defined in ac_api.cu)
 int set_error(int code, const char *msg);
 
+// One-time, per-device set-up of a kernel that takes `smem` bytes of
+// dynamic shared memory: raises its dynamic shared-memory limit and returns
+// in *occ the CTAs of `threads` threads that fit on one SM (at least 1).
+// Each kernel keeps one KernelSetup (a static of its launcher); the first
+// launch on a device does the set-up under a process-wide mutex and
+// publishes the result with release semantics, later launches read it
+// without locking.  Devices beyond the cache are set up on every launch.
+// Safe to call from several host threads at once.
+constexpr int kSetupDevices = 64;
+struct KernelSetup {
+  std::atomic<int> occ[kSetupDevices];  // 0 = not set up on that device yet
+};
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ);
+
 }  // namespace ac
 
 #include <vector>
@@ -79,6 +115,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 int ac_validate_desc(const ac_grid_desc *d);
+int ac_default_depth(int ndim, int dtype);  // temporal-block depth of the default schedule
 bool ac_plan_depths(int64_t n, int k, std::vector<int> &depths);
 EncodeTiledFn ac_encode_fn();
 CUtensorMapDataType ac_tmap_type(int dtype);

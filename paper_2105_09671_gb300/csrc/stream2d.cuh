@@ -33,16 +33,21 @@ namespace ac {
 constexpr int kS2Warps = 8;   // warps per CTA (independent strips)
 constexpr int kS2Stages = 6;  // ring depth per warp
 constexpr int kS2Rows = 2;    // rows per TMA box
+constexpr int kS2Tiles = 2;   // strip widths (tile 0: S2Cfg::VPL vectors per lane, tile 1: two)
 
+// VPL = 16-byte vectors per lane (tile 0).  FP32 also offers strips twice
+// as wide (tile 1: two vectors, 8 cells per lane: half the shuffles and
+// x-face selects per cell and half the strip-halo share, for more
+// registers; depths up to KMAX_WIDE).
 template <typename T> struct S2Cfg;
-template <> struct S2Cfg<float> { static constexpr int VPL = 1, KMAX = 8; };
-template <> struct S2Cfg<double> { static constexpr int VPL = 2, KMAX = 8; };
-template <> struct S2Cfg<__half> { static constexpr int VPL = 1, KMAX = 6; };
+template <> struct S2Cfg<float> { static constexpr int VPL = 1, KMAX = 8, KMAX_WIDE = 6; };
+template <> struct S2Cfg<double> { static constexpr int VPL = 2, KMAX = 8, KMAX_WIDE = 0; };
+template <> struct S2Cfg<__half> { static constexpr int VPL = 1, KMAX = 6, KMAX_WIDE = 0; };
 
-template <typename T, int K>
+template <typename T, int K, int VPL_ = S2Cfg<T>::VPL>
 struct S2Geom {
   static constexpr int V = Traits<T>::V;
-  static constexpr int VPL = S2Cfg<T>::VPL;
+  static constexpr int VPL = VPL_;
   static constexpr int E = V * VPL;                 // cells per lane
   static constexpr int SW = 32 * E;                 // strip width (cells)
   static constexpr int HX = V * ((K + V - 1) / V);  // halo per side, vector aligned
@@ -65,12 +70,12 @@ struct S2Item {
 // warp has consumed so far (stage u % D, phase (u / D) & 1) and is advanced
 // past this item.  Returns false if a bounded wait expired (the status word
 // is set and every copy this item issued has landed).
-template <typename T, int K, bool FASTX>
+template <typename T, int K, bool FASTX, int VPL_ = S2Cfg<T>::VPL>
 __device__ __forceinline__ bool s2_item(T *ring_smem, uint64_t *bars, uint32_t &u,
                                         const CUtensorMap *src_map, T *__restrict__ dst,
                                         const S2Item &it, typename Traits<T>::C alpha,
                                         typename Traits<T>::C beta, int *status) {
-  using Gm = S2Geom<T, K>;
+  using Gm = S2Geom<T, K, VPL_>;
   using C = typename Traits<T>::C;
   constexpr int E = Gm::E, V = Gm::V, VPL = Gm::VPL, D = kS2Stages;
   constexpr uint32_t kStageBytes = Gm::STAGE_ELEMS * sizeof(T);
@@ -244,24 +249,24 @@ struct S2Ring {
   T *smem;
   uint64_t *bars;
 };
-template <typename T, int K>
+template <typename T, int K, int VPL_ = S2Cfg<T>::VPL>
 __device__ __forceinline__ S2Ring<T> s2_ring(unsigned char *smem, int warp) {
-  using Gm = S2Geom<T, K>;
+  using Gm = S2Geom<T, K, VPL_>;
   S2Ring<T> r;
   r.smem = reinterpret_cast<T *>(smem + warp * Gm::RING_BYTES);
   r.bars = reinterpret_cast<uint64_t *>(smem + kS2Warps * Gm::RING_BYTES) + warp * kS2Stages;
   return r;
 }
 
-template <typename T, int K, bool FASTX>
+template <typename T, int K, bool FASTX, int VPL_>
 __global__ void __launch_bounds__(kS2Warps * 32, 1)
     stream2d_k(const __grid_constant__ CUtensorMap src_map, T *__restrict__ dst, GridParams g,
                int n_strips, int n_chunks, int chunk_rows) {
-  using Gm = S2Geom<T, K>;
+  using Gm = S2Geom<T, K, VPL_>;
   using C = typename Traits<T>::C;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const S2Ring<T> ring = s2_ring<T, K>(smem, warp);
+  const S2Ring<T> ring = s2_ring<T, K, VPL_>(smem, warp);
 
   const int64_t gw = (int64_t)blockIdx.x * kS2Warps + warp;
   if (gw >= (int64_t)n_strips * n_chunks) return;  // no CTA-wide barrier in this kernel
@@ -283,37 +288,25 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
   }
   __syncwarp();
   uint32_t u = 0;
-  s2_item<T, K, FASTX>(ring.smem, ring.bars, u, &src_map, dst, it, (C)g.alpha, (C)g.beta, g.status);
+  s2_item<T, K, FASTX, VPL_>(ring.smem, ring.bars, u, &src_map, dst, it, (C)g.alpha, (C)g.beta, g.status);
 }
 
 // ------------------------------------------------------------------ host ---
 
-template <typename T, int K>
+template <typename T, int K, int VPL_>
 inline Stream2DGeom s2_geom_t() {
-  using Gm = S2Geom<T, K>;
+  using Gm = S2Geom<T, K, VPL_>;
   return Stream2DGeom{Gm::SW, kS2Rows, Gm::HX, Gm::OW};
 }
 
-template <typename T, int K, bool FASTX>
+template <typename T, int K, bool FASTX, int VPL_>
 static cudaError_t s2_launch_t(const GridParams &g, const CUtensorMap *map, void *dst, int num_sms,
                                cudaStream_t s) {
-  using Gm = S2Geom<T, K>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static unsigned attr_mask = 0;
-  static int occ_cache[32] = {0};
-  if (dev < 32 && !(attr_mask & (1u << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(stream2d_k<T, K, FASTX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream2d_k<T, K, FASTX>, kS2Warps * 32,
-                                                      Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    occ_cache[dev] = std::max(1, occ);
-    attr_mask |= 1u << dev;
-  }
-  const int occ = dev < 32 ? occ_cache[dev] : 1;
+  using Gm = S2Geom<T, K, VPL_>;
+  static KernelSetup ks;
+  int occ = 1;
+  cudaError_t e = kernel_setup(ks, (const void *)stream2d_k<T, K, FASTX, VPL_>, kS2Warps * 32, Gm::SMEM, &occ);
+  if (e != cudaSuccess) return e;
   const int n_strips = (int)((g.nx + Gm::OW - 1) / Gm::OW);
   // one wave of resident warps, but chunks of at least max(16, 3k) rows so
   // that the 2k halo rows per chunk stay a modest overhead
@@ -325,21 +318,28 @@ static cudaError_t s2_launch_t(const GridParams &g, const CUtensorMap *map, void
   n_chunks = (int)((g.ny + chunk_rows - 1) / chunk_rows);
   const int64_t warps = (int64_t)n_strips * n_chunks;
   const unsigned blocks = (unsigned)((warps + kS2Warps - 1) / kS2Warps);
-  stream2d_k<T, K, FASTX><<<blocks, kS2Warps * 32, Gm::SMEM, s>>>(*map, (T *)dst, g, n_strips,
-                                                                  n_chunks, chunk_rows);
+  stream2d_k<T, K, FASTX, VPL_><<<blocks, kS2Warps * 32, Gm::SMEM, s>>>(*map, (T *)dst, g, n_strips,
+                                                                        n_chunks, chunk_rows);
   return cudaGetLastError();
 }
 
+// Depths available for a storage type and tile (0: VPL of S2Cfg, 1: twice as wide).
 template <typename T>
+constexpr int s2_kmax(int tile) {
+  return tile == 0 ? S2Cfg<T>::KMAX : tile == 1 ? S2Cfg<T>::KMAX_WIDE : 0;
+}
+
+template <typename T, int VPL_>
 cudaError_t s2_dispatch(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms,
                         cudaStream_t s) {
+  constexpr int KMAX = VPL_ == S2Cfg<T>::VPL ? S2Cfg<T>::KMAX : S2Cfg<T>::KMAX_WIDE;
   const bool fastx = g.nx % Traits<T>::V == 0;
   switch (k) {
-#define AC_CASE(KK)                                                           \
-  case KK:                                                                    \
-    if constexpr (KK <= S2Cfg<T>::KMAX)                                       \
-      return fastx ? s2_launch_t<T, KK, true>(g, map, dst, num_sms, s)        \
-                   : s2_launch_t<T, KK, false>(g, map, dst, num_sms, s);      \
+#define AC_CASE(KK)                                                                \
+  case KK:                                                                         \
+    if constexpr (KK <= KMAX)                                                      \
+      return fastx ? s2_launch_t<T, KK, true, VPL_>(g, map, dst, num_sms, s)       \
+                   : s2_launch_t<T, KK, false, VPL_>(g, map, dst, num_sms, s);     \
     break;
     AC_CASE(1) AC_CASE(2) AC_CASE(3) AC_CASE(4) AC_CASE(5) AC_CASE(6) AC_CASE(7) AC_CASE(8)
 #undef AC_CASE
@@ -347,12 +347,13 @@ cudaError_t s2_dispatch(int k, const GridParams &g, const CUtensorMap *map, void
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, int VPL_>
 Stream2DGeom s2_geom(int k) {
+  constexpr int KMAX = VPL_ == S2Cfg<T>::VPL ? S2Cfg<T>::KMAX : S2Cfg<T>::KMAX_WIDE;
   switch (k) {
 #define AC_CASE(KK) \
   case KK:          \
-    if constexpr (KK <= S2Cfg<T>::KMAX) return s2_geom_t<T, KK>(); \
+    if constexpr (KK <= KMAX) return s2_geom_t<T, KK, VPL_>(); \
     break;
     AC_CASE(1) AC_CASE(2) AC_CASE(3) AC_CASE(4) AC_CASE(5) AC_CASE(6) AC_CASE(7) AC_CASE(8)
 #undef AC_CASE
@@ -362,6 +363,7 @@ Stream2DGeom s2_geom(int k) {
 
 cudaError_t stream2d_launch_f64(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
 cudaError_t stream2d_launch_f32(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
+cudaError_t stream2d_launch_f32_wide(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
 cudaError_t stream2d_launch_f16(int k, const GridParams &g, const CUtensorMap *map, void *dst, int num_sms, cudaStream_t s);
 
 }  // namespace ac

@@ -39,6 +39,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -52,29 +53,39 @@ namespace ac {
 // TMA box (the halo tile) is at most 256 elements in x.
 constexpr int kS3Tiles = 3;
 template <typename T, int TILE> struct S3Cfg;
+// VL = cells per thread vector: one 16-byte vector (FP16 storage: 8
+// cells).  Half vectors for FP16 storage (VL = 4, 8-byte loads, FP32's
+// thread count and registers) were measured slower on GB300 at 512^3 (k = 2
+// tile 0: 995 against 1054 Gcell-updates/s): more threads repeat the
+// per-plane work, and the 16-byte TMA alignment widens the x halo to 8.
 template <int TILE> struct S3Cfg<float, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
   static constexpr int DK = TILE == 0 ? 6 : 3;  // TMA stages at k >= 2
+  static constexpr int VL = 4;
 };
 template <int TILE> struct S3Cfg<double, TILE> {
   static constexpr int OX = 64, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 4 : 2, KMAX = 2, MINB = TILE == 1 ? 2 : 1;
   static constexpr int DK = 3;
+  static constexpr int VL = 2;
 };
 template <int TILE> struct S3Cfg<__half, TILE> {
   static constexpr int OX = 128, OY = TILE == 1 ? 16 : 32;
   static constexpr int R = TILE == 2 ? 1 : 2, KMAX = 3, MINB = TILE == 1 ? 2 : 1;
   static constexpr int DK = 3;
+  static constexpr int VL = 8;
 };
 
 template <typename T, int K, int TILE = 0>
 struct S3Geom {
   using Cfg = S3Cfg<T, TILE>;
   using C = typename Traits<T>::C;
-  static constexpr int V = Traits<T>::V;
+  static constexpr int V = Cfg::VL;                       // cells per thread vector
+  static constexpr int VA = 16 / (int)sizeof(T);          // TMA x alignment (elements)
+  static constexpr int HA = V > VA ? V : VA;
   static constexpr int R = Cfg::R, MINB = Cfg::MINB;
-  static constexpr int HX = V * ((K + V - 1) / V);
+  static constexpr int HX = HA * ((K + HA - 1) / HA);     // halo columns, both alignments
   static constexpr int OX = Cfg::OX, OY = Cfg::OY;
   static constexpr int TX = OX + 2 * HX, TXV = TX / V;
   static constexpr int TY = (OY + 2 * K + R - 1) / R * R;  // rows, whole groups of R
@@ -100,9 +111,32 @@ struct S3Geom {
   static_assert(TY <= 256 && TX <= 256, "TMA box limits");
 };
 
+// V storage elements (16 or 8 bytes) <-> V compute values.
 template <typename T, int V>
 __device__ __forceinline__ void ld_vec(const T *buf, int idx, typename Traits<T>::C *out) {
-  unpack16<T>(*reinterpret_cast<const uint4 *>(buf + idx), out);
+  if constexpr (sizeof(T) * V == 16) {
+    unpack16<T>(*reinterpret_cast<const uint4 *>(buf + idx), out);
+  } else {
+    static_assert(std::is_same_v<T, __half> && V == 4, "8-byte vectors are FP16 storage");
+    const uint2 w = *reinterpret_cast<const uint2 *>(buf + idx);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&w.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&w.y));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_vec_g(T *p, const typename Traits<T>::C *in, bool pred) {
+  if constexpr (sizeof(T) * V == 16) {
+    const uint4 pk = pack16<T>(in);
+    if (pred) *reinterpret_cast<uint4 *>(p) = pk;
+  } else {
+    static_assert(std::is_same_v<T, __half> && V == 4, "8-byte vectors are FP16 storage");
+    const __half2 a = __floats2half2_rn(in[0], in[1]), b = __floats2half2_rn(in[2], in[3]);
+    uint2 pk;
+    pk.x = *reinterpret_cast<const uint32_t *>(&a);
+    pk.y = *reinterpret_cast<const uint32_t *>(&b);
+    if (pred) *reinterpret_cast<uint2 *>(p) = pk;
+  }
 }
 template <int V>
 __device__ __forceinline__ void ld_vec_c(const float *buf, int idx, float *out) {
@@ -237,16 +271,21 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       constexpr int LW = P % 3, LR = (P + 2) % 3;
       // Shared-memory reads of level 0: the stage of plane t-1 (level l >= 1
       // reads the level-l plane of the previous iteration in its own turn).
+      // At t == 0 there is no plane t-1: that stage may still be receiving
+      // the prologue's TMA load, so it is not read (the values would only
+      // feed plane lo0-1, which lies outside every output cone).
       C ys[K][V], yn[K][V], ev[K][R];
+      if (P != 0 || t > 0) {
+        const T *cb = stage_ptr(SPREV);
+        ld_vec<T, V>(cb, ysn, ys[0]);
+        ld_vec<T, V>(cb, ynn, yn[0]);
 #pragma unroll
-      for (int l = 0; l < K; ++l) {
-        if (l == 0) {
-          const T *cb = stage_ptr(SPREV);
-          ld_vec<T, V>(cb, ysn, ys[0]);
-          ld_vec<T, V>(cb, ynn, yn[0]);
+        for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
+      } else {
 #pragma unroll
-          for (int i = 0; i < R; ++i) ev[0][i] = esm ? to_c(cb[eoff + i * TX]) : C(0);
-        }
+        for (int e = 0; e < V; ++e) ys[0][e] = yn[0][e] = C(0);
+#pragma unroll
+        for (int i = 0; i < R; ++i) ev[0][i] = C(0);
       }
       bool ok = true;
       if (!BND || t < n_in) {
@@ -329,8 +368,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
             T *d = dst + (int64_t)ZK * plane_stride + goff + (int64_t)i * g.pitch;
             const bool sv = store && st_row[i];
             if (FASTX || st_full) {  // (FASTX: nx % V == 0, every vector is whole)
-              const uint4 pk = pack16<T>(out);
-              if (sv) *reinterpret_cast<uint4 *>(d) = pk;
+              st_vec_g<T, V>(d, out, sv);
             } else if (sv) {
 #pragma unroll
               for (int e = 0; e < V; ++e)
@@ -415,21 +453,10 @@ template <typename T, int K, bool FASTX, int TILE>
 static cudaError_t s3_launch_t(const GridParams &g, const CUtensorMap *map, void *dst, int num_sms,
                                cudaStream_t s) {
   using Gm = S3Geom<T, K, TILE>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static unsigned attr_mask = 0;
-  static int occ_cache[32] = {0};
-  if (dev < 32 && !(attr_mask & (1u << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(stream3d_k<T, K, FASTX, TILE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream3d_k<T, K, FASTX, TILE>, Gm::NT, Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    occ_cache[dev] = std::max(1, occ);
-    attr_mask |= 1u << dev;
-  }
-  const int occ = dev < 32 ? occ_cache[dev] : 1;
+  static KernelSetup ks;
+  int occ = 1;
+  cudaError_t e = kernel_setup(ks, (const void *)stream3d_k<T, K, FASTX, TILE>, Gm::NT, Gm::SMEM, &occ);
+  if (e != cudaSuccess) return e;
   const int tiles_x = (int)((g.nx + Gm::OX - 1) / Gm::OX);
   const int tiles_y = (int)((g.ny + Gm::OY - 1) / Gm::OY);
   const int64_t tiles = (int64_t)tiles_x * tiles_y;
@@ -459,7 +486,7 @@ static cudaError_t s3_launch_t(const GridParams &g, const CUtensorMap *map, void
 template <typename T, int TILE>
 cudaError_t s3_dispatch_tile(int k, const GridParams &g, const CUtensorMap *map, void *dst,
                              int num_sms, cudaStream_t s) {
-  const bool fastx = g.nx % Traits<T>::V == 0;
+  const bool fastx = g.nx % S3Cfg<T, TILE>::VL == 0;
   switch (k) {
     case 1:
       return fastx ? s3_launch_t<T, 1, true, TILE>(g, map, dst, num_sms, s)

@@ -19,10 +19,11 @@ def schedules(ndim: int, dtype: str):
     """Every (variant, k, tile) the library accepts for this grid kind."""
     from paper_2105_09671_gb300 import _lib as L
     out = [(L.AC_VARIANT_DIRECT, 1, 0)]
-    kmax = {(2, "f64"): 8, (2, "f32"): 8, (2, "f16s"): 6, (3, "f64"): 2, (3, "f32"): 3, (3, "f16s"): 3}
-    tiles = L.AC_NUM_TILES_3D if ndim == 3 else 1
-    for k in range(1, kmax[(ndim, dtype)] + 1):
-        for tile in range(tiles):
+    # deepest k per (grid kind, storage type, tile)
+    kmax = {(2, "f64"): [8], (2, "f32"): [8, 6], (2, "f16s"): [6],
+            (3, "f64"): [2, 2, 2], (3, "f32"): [3, 3, 3], (3, "f16s"): [3, 3, 3]}
+    for tile, km in enumerate(kmax[(ndim, dtype)]):
+        for k in range(1, km + 1):
             out.append((L.AC_VARIANT_STREAM, k, tile))
     return out
 

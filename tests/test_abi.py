@@ -87,3 +87,33 @@ def test_null_context_calls_fail_cleanly():
     assert lib.ac_destroy(None) == ac.AC_OK
     x = ctypes.c_double()
     assert lib.ac_energy(None, ctypes.byref(x)) == ac.AC_ERR_INVALID
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # sizeof / offsetof of every public struct, from a C compiler reading
+    # include/ac.h, against the ctypes mirrors of the binding
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ac_grid_desc": L.AcGridDesc, "ac_guard": L.AcGuard, "ac_train_config": L.AcTrainConfig,
+               "ac_learned_report": L.AcLearnedReport, "ac_guard_calibration": L.AcGuardCalibration}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, f"{cname}.{fname}"

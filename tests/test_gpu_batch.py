@@ -81,6 +81,44 @@ def test_batch_uneven_workload_2000_steps_against_oracle():
         assert float(np.max(np.abs(got[i] - o))) <= 1e-4
 
 
+def test_batched_workload_sampled_instances_against_oracle():
+    # the batched workload itself: 512 uneven grids (64^2 .. 1024^2, eps 3h..6h,
+    # circles and random states), autotuned depth, graph-replayed, 2000 steps;
+    # 16 instances drawn at random are compared with the FP64 oracle
+    import torch
+    inst = wl.batch_instances(512, seed=0)
+    specs = [((d["n"], d["n"]), d["h"], d["eps"], d["dt"]) for d in inst]
+    inits = []
+    for d in inst:
+        shp = (d["n"], d["n"])
+        inits.append(oracle.init_sphere(shp, d["h"], d["r0"], d["eps"]) if d["init"] == "sphere"
+                     else oracle.init_random(shp, seed=d["seed"]))
+    s = torch.cuda.Stream()
+    b = ac.Batch(specs, dtype="f32", stream=s)
+    sample = np.random.default_rng(2024).choice(len(inst), size=16, replace=False)
+    try:
+        for i, a in enumerate(inits):
+            b.load(i, a)
+        b.autotune(64)  # restores the fields it times on
+        k = b.schedule()
+        assert 1 <= k <= 4
+        b.set_graph(True)
+        b.step(2000)
+        assert b.status() == ac.AC_OK
+        got = {int(i): b.to_numpy(int(i)).astype(np.float64) for i in sample}
+    finally:
+        b.close()
+    worst = 0.0
+    for i in sample:
+        d = inst[int(i)]
+        o = oracle.step(stored(inits[int(i)], "f32"), d["h"], d["eps"], d["dt"], 2000)
+        rel = float(np.linalg.norm(got[int(i)] - o) / np.linalg.norm(o))
+        worst = max(worst, rel)
+        assert rel <= 1e-3, f"instance {i} (n = {d['n']}): rel-L2 {rel:.2e}"
+        assert float(np.max(np.abs(got[int(i)] - o))) <= 1e-4
+    print(f"\nbatch512: autotuned k = {k}; 16 sampled instances, worst rel-L2 {worst:.2e}")
+
+
 def test_batch_graph_replay_and_launch_count():
     import torch
     specs, inits = _specs(SHAPES[2:6], seed=3)

@@ -142,47 +142,145 @@ def test_jump_residual_of_the_plain_stepper():
     assert 0 < vals["sphere"] < vals["random"]
 
 
-def test_what_the_trained_network_gains_over_the_plain_stepper():
-    """Train a 2D network on 64^2 trajectories, advance a 128^2 circle by 40
-    guarded jumps (640 steps) and report time and error against the plain
-    stepper and the FP64 oracle.  Measured on GB300: the hybrid is about 3x
-    slower than the plain stepper here and about 2e-2 relative L2 from the
-    oracle (the 1e-3 target is not met; the plain stepper is at 2e-7).  The
-    assertions bound that outcome as a regression check: the guard keeps the
-    field in [-1.001, 1.001] and the error below 5e-2."""
+@pytest.mark.parametrize("shape", [(128, 128), (200, 130), (40, 40), (24, 24, 24), (64, 48, 40)])
+def test_spot_check_reproduces_the_plain_stepper(shape):
+    # the spot check recomputes the plain stepper's 16-step result on boxes;
+    # for a jump made by the plain stepper itself it must find no difference
+    # at all (same FP32 arithmetic), whether the boxes sit inside the grid,
+    # touch its faces, or cover it (40^2, 24^3: boxes clipped to the grid)
+    s = _stream()
+    n = max(shape)
+    h = 1.0 / n
+    a = ac.Simulation(shape, h, 4 * h, 0.1 * h * h, dtype="f32", stream=s)
+    b = ac.Simulation(shape, h, 4 * h, 0.1 * h * h, dtype="f32", stream=s)
+    try:
+        a.init_random(seed=3)
+        b.init_random(seed=3)
+        b.step(16)
+        for seed in (7, 8):
+            mx, rel, cells = L.ac_jump_spot_check(a.ctx, b._buf.data_ptr(), 16, 0, 0, seed)
+            assert mx == 0.0 and rel == 0.0
+            assert cells > 0
+        if shape in ((40, 40), (24, 24, 24)):
+            # every default box (64 in 2D, 16 in 3D) clips to the whole grid
+            assert cells == np.prod(shape) * (64 if len(shape) == 2 else 16)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_spot_check_measures_planted_errors():
+    import torch
+    s = _stream()
+    n = 40  # boxes of 32 + 2 * 16 cells clip to the whole 40^2 grid: every cell is checked
+    h = 1.0 / n
+    a = ac.Simulation((n, n), h, 4 * h, 0.1 * h * h, dtype="f32", stream=s)
+    b = ac.Simulation((n, n), h, 4 * h, 0.1 * h * h, dtype="f32", stream=s)
+    try:
+        a.init_sphere(r0=0.3)
+        b.init_sphere(r0=0.3)
+        b.step(16)
+        with torch.cuda.stream(s):
+            ref = b.phi.clone()
+            b.phi.mul_(1.0 + 1e-3)  # a uniform relative error of 1e-3
+        mx, rel, _ = L.ac_jump_spot_check(a.ctx, b._buf.data_ptr(), 16, 1, 0, 1)
+        assert abs(rel - 1e-3) <= 1e-6
+        with torch.cuda.stream(s):
+            b.phi.copy_(ref)
+            b.phi[n - 1, 0] += 0.5  # one wrong cell in a corner of the domain
+        mx, rel, _ = L.ac_jump_spot_check(a.ctx, b._buf.data_ptr(), 16, 1, 0, 1)
+        assert mx == pytest.approx(0.5, abs=1e-6)
+        assert rel > 0
+    finally:
+        a.close()
+        b.close()
+
+
+def _trained_net(s):
+    net = L.ac_net_create(2, s.cuda_stream)
+    cfg = L.AcTrainConfig(n=64, eps_cells=4.0, pool=16, trajectory_jumps=40, iterations=600,
+                          steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=11)
+    L.ac_net_train(net, cfg)
+    return net
+
+
+def test_calibration_sets_the_residual_threshold():
+    s = _stream()
+    net = _trained_net(s)
+    try:
+        cal = L.AcTrainConfig(n=64, eps_cells=4.0, pool=16, trajectory_jumps=40, iterations=1,
+                              steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=12345)
+        guard = L.AcGuard(16, 1e-6, 1.001, 0.0, 0.0, 0, 0, 99)
+        rep = L.ac_net_calibrate_guard(net, cal, 2.0, guard)
+        print(f"\ncalibration: {rep}")
+        assert rep["states"] == 16
+        assert rep["plain_residual_max"] > 0
+        assert guard.residual_tol == pytest.approx(2.0 * rep["plain_residual_max"], rel=1e-12)
+        assert 0 < rep["net_rel_err_median"] <= rep["net_rel_err_max"]
+        # on 64^2 the spot check's boxes cover the whole grid: its estimate is
+        # the whole-field error (up to the order of the sums)
+        assert rep["spot_rel_err_max"] == pytest.approx(rep["net_rel_err_max"], rel=1e-9)
+    finally:
+        L.ac_net_destroy(net)
+
+
+@pytest.mark.parametrize("init", ["circle", "random"])
+def test_guarded_learned_stepper_meets_the_target_or_falls_back(init):
+    """A trained network advances a 128^2 field by 40 guarded jumps (640
+    steps); the guard's spot check allows each jump a relative error of
+    1e-3 / 40 against the plain stepper (the final target over the jumps),
+    so the result must be within 1e-3 relative L2 of the FP64 oracle,
+    whether the jumps are accepted or fall back.  Measured on GB300 with
+    this small network: every jump is rejected on both states (its
+    per-jump errors are ~1e-3 on the circle and up to ~0.6 on the random
+    state), the result is the plain stepper's (~2e-7 from the oracle), and
+    the hybrid is slower than the plain stepper.  Without the spot check
+    the random state's error grows to ~1.5: the guard is what keeps it."""
     import time
     import torch
     s = _stream()
-    net = L.ac_net_create(2, s.cuda_stream)
-    n = 128
+    net = _trained_net(s)
+    n, jumps = 128, 40
     h = 1.0 / n
+    target = 1e-3
     try:
-        cfg = L.AcTrainConfig(n=64, eps_cells=4.0, pool=16, trajectory_jumps=40, iterations=600,
-                              steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=11)
-        L.ac_net_train(net, cfg)
-        phi0 = oracle.init_sphere((n, n), h, 0.3, 4 * h)
-        ref = oracle.step(phi0.astype(np.float32).astype(np.float64), h, 4 * h, 0.1 * h * h, 640)
+        cal = L.AcTrainConfig(n=64, eps_cells=4.0, pool=16, trajectory_jumps=40, iterations=1,
+                              steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=12345)
+        guard = L.AcGuard(16, 1e-6, 1.001, 0.0, target / jumps, 0, 0, 99)
+        L.ac_net_calibrate_guard(net, cal, 2.0, guard)
+        assert guard.residual_tol > 0
+        phi0 = (oracle.init_sphere((n, n), h, 0.3, 4 * h) if init == "circle"
+                else oracle.init_random((n, n), seed=5))
+        ref = oracle.step(phi0.astype(np.float32).astype(np.float64), h, 4 * h, 0.1 * h * h, 16 * jumps)
         res = {}
-        for mode in ("learned", "plain"):
+        for mode in ("learned", "unguarded", "plain"):
             sim = ac.Simulation((n, n), h, 4 * h, 0.1 * h * h, dtype="f32", stream=s)
             try:
                 sim.load(phi0)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                fb = None
+                rep = None
                 if mode == "learned":
-                    fb = L.ac_learned_advance(sim.ctx, net, 40, L.AcGuard(16, 1e-6, 1.001, 0.0))
+                    _, rep = L.ac_learned_advance(sim.ctx, net, jumps, guard, with_report=True)
+                elif mode == "unguarded":
+                    _, rep = L.ac_learned_advance(sim.ctx, net, jumps, L.AcGuard(16, 1e30, 1e30, 0.0),
+                                                  with_report=True)
                 else:
-                    sim.step(640)
+                    sim.step(16 * jumps)
                 s.synchronize()
                 dt = time.perf_counter() - t0
                 out = sim.to_numpy().astype(np.float64)
             finally:
                 sim.close()
-            res[mode] = (dt, fb, float(np.linalg.norm(out - ref) / np.linalg.norm(ref)))
-        print(f"learned: {res['learned'][0]*1e3:.2f} ms, {res['learned'][1]} fallbacks, rel-L2 {res['learned'][2]:.2e}; "
-              f"plain: {res['plain'][0]*1e3:.2f} ms, rel-L2 {res['plain'][2]:.2e}")
+            res[mode] = (dt, rep, float(np.linalg.norm(out - ref) / np.linalg.norm(ref)))
+        rl = res["learned"][1]
+        print(f"\n{init}: learned {res['learned'][0]*1e3:.2f} ms, {rl['fallbacks']}/{jumps} fallbacks "
+              f"(spot {rl['rejected_spot']}, energy {rl['rejected_energy']}, max {rl['rejected_max_abs']}, "
+              f"residual {rl['rejected_residual']}), largest spot error {rl['max_spot_rel']:.2e}, "
+              f"rel-L2 {res['learned'][2]:.2e}; unguarded rel-L2 {res['unguarded'][2]:.2e}; "
+              f"plain {res['plain'][0]*1e3:.2f} ms, rel-L2 {res['plain'][2]:.2e}")
         assert res["plain"][2] <= 1e-5
-        assert res["learned"][2] <= 5e-2
+        assert res["learned"][2] <= target
+        assert rl["jumps"] == jumps
     finally:
         L.ac_net_destroy(net)

@@ -13,6 +13,38 @@ pytestmark = pytest.mark.gpu
 TOL_OUT = 3e-2
 TOL_GRAD = 6e-2
 
+# Per-element bounds.  Every layer rounds its activations and its 32 -> 32
+# weights to BF16 (relative error <= 2^-9 each, round to nearest) and sums
+# in FP32.  A cell's output is a sum of many such rounded products whose
+# errors are independent, so its error is about 2^-9 times the RMS size of
+# the terms, times sqrt(2 * 6) for the roundings of six layers: ~1.7 * 2^-8
+# of the output's RMS, and some 4 sigma of that over 10^4 cells.  Where the
+# output is near zero (terms cancelling) the RMS part of the bound covers it:
+#   |gpu - oracle| <= C * 2^-8 * (|oracle| + RMS(oracle))
+# with C_OUT = 8 for the jump increment.  A wrong tap or a wrong replicated
+# boundary cell changes a cell by O(RMS), i.e. a ratio near 0.5, far above
+# 8 * 2^-8 = 0.031.
+# Weight gradients dW[t][ci][co] = sum_p a[p+t][ci] g[p][co] multiply the
+# forward activations (error up to C_OUT * 2^-8 of their RMS) by the
+# backward signal, which carries the loss residual's share of the forward
+# error and, per layer, the BF16 roundings of the data gradient, of the
+# pre-activation inside gelu' and of the transposed weights: about
+# 5 * 2^-8 relative per product term.  With random data the terms of a sum
+# have random signs, so a gradient entry keeps that relative error (it does
+# not average down against the entry's own size), and the largest of ~10^4
+# entries sits near 4 sigma, ~20 * 2^-8 of the layer's RMS: C_GRAD = 32.  A
+# wrong tap or a wrong replicate-padding adjoint shows on the grids made of
+# boundary cells only (3 x 1, 1 x 130, 2 x 2 x 2) as errors of the order of
+# the entries themselves, C > 100.
+C_OUT = 8.0
+C_GRAD = 32.0
+
+
+def _elementwise_ratio(got, ref):
+    """max |got - ref| / (2^-8 (|ref| + RMS(ref))): the C the bound needs."""
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    return float(np.max(np.abs(got - ref) / (2.0 ** -8 * (np.abs(ref) + rms + 1e-300))))
+
 
 def _params(ndim, seed):
     p = onet.init_params(ndim, seed=seed)
@@ -40,7 +72,8 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30))
 
 
-CASES = [(2, (2, 17, 200)), (2, (1, 64, 64)), (2, (1, 3, 1)), (3, (1, 5, 9, 130)), (3, (2, 4, 4, 4))]
+CASES = [(2, (2, 17, 200)), (2, (1, 64, 64)), (2, (1, 3, 1)), (2, (1, 1, 130)), (3, (1, 5, 9, 130)),
+         (3, (2, 4, 4, 4)), (3, (1, 2, 2, 2))]
 
 
 def _shape_args(ndim, shape):
@@ -72,7 +105,12 @@ def test_forward_matches_oracle(ndim, shape):
         L.ac_net_destroy(h)
     phi32 = phi.astype(np.float32).astype(np.float64)
     # compare the learned increments (output minus input) / scale
-    assert _rel((out - phi32) / scale, (ref - phi) / scale) <= TOL_OUT
+    inc_gpu, inc_ref = (out - phi32) / scale, (ref - phi) / scale
+    assert _rel(inc_gpu, inc_ref) <= TOL_OUT
+    # and cell by cell, so that one wrong tap or boundary cell cannot hide
+    ratio = _elementwise_ratio(inc_gpu, inc_ref)
+    print(f"\nforward {ndim}D {shape}: per-element C = {ratio:.2f} (bound {C_OUT})")
+    assert ratio <= C_OUT
 
 
 @pytest.mark.parametrize("ndim,shape", CASES)
@@ -96,9 +134,16 @@ def test_loss_and_gradients_match_oracle(ndim, shape):
         L.ac_net_destroy(h)
     assert loss == pytest.approx(loss_ref, rel=TOL_OUT)
     got = _unflat(g.astype(np.float64), params)
+    ratios = {}
     for li, ((gw, gb), (rw, rb)) in enumerate(zip(got, grads_ref)):
         assert _rel(gw, rw) <= TOL_GRAD, f"layer {li} weights"
         assert _rel(gb, rb) <= TOL_GRAD, f"layer {li} bias"
+        ratios[f"w{li}"] = _elementwise_ratio(gw, rw)
+        ratios[f"b{li}"] = _elementwise_ratio(gb, rb)
+    print(f"\ngradients {ndim}D {shape}: per-element C " +
+          " ".join(f"{k}={v:.2f}" for k, v in ratios.items()) + f" (bound {C_GRAD})")
+    bad = {k: v for k, v in ratios.items() if v > C_GRAD}
+    assert not bad, f"per-element bound exceeded: {bad}"
 
 
 def test_adam_training_lowers_the_loss():

@@ -194,11 +194,17 @@ def test_mirror_symmetry_3d_every_tile():
 def test_tile_selection_api():
     sim2 = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim3 = ac.Simulation((8, 16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
+    sim2h = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f16s")
     try:
         assert sim2.tile() == 0
         sim2.set_tile(0)
+        sim2.set_tile(1)             # FP32 2D: strips of 8 cells per lane
+        assert sim2.tile() == 1
         with pytest.raises(ac.AcError) as e:
-            sim2.set_tile(1)
+            sim2.set_tile(ac.AC_NUM_TILES_2D)
+        assert e.value.code == ac.AC_ERR_INVALID
+        with pytest.raises(ac.AcError) as e:
+            sim2h.set_tile(1)        # FP16 storage has one strip width
         assert e.value.code == ac.AC_ERR_UNSUPPORTED
         with pytest.raises(ac.AcError) as e:
             sim3.set_tile(ac.AC_NUM_TILES_3D)
@@ -212,6 +218,7 @@ def test_tile_selection_api():
         sim3.set_tile(ac.AC_TILE_AUTO)
         assert sim3.tile() in range(ac.AC_NUM_TILES_3D)
     finally:
+        sim2h.close()
         sim2.close()
         sim3.close()
 

@@ -30,7 +30,7 @@ def test_autotune_keeps_field_and_steps_correctly(shape, dtype):
         v, k = sim.schedule()
         tile = sim.tile()
         assert v in (ac.AC_VARIANT_DIRECT, ac.AC_VARIANT_STREAM) and 1 <= k <= ac.AC_MAX_K
-        assert 0 <= tile < (ac.AC_NUM_TILES_3D if len(shape) == 3 else 1)
+        assert 0 <= tile < (ac.AC_NUM_TILES_3D if len(shape) == 3 else ac.AC_NUM_TILES_2D)
         sim.step(23)
         assert sim.status() == ac.AC_OK
         out = sim.to_numpy().astype(np.float64)

@@ -29,7 +29,10 @@ def test_rejects_grids_beyond_the_scratch_limit():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dtype,shape", [("f32", (300, 257)), ("f64", (31, 40, 77)),
-                                         ("f16s", (64, 64)), ("f32", (512, 512, 512))])
+                                         ("f16s", (64, 64)), ("f32", (512, 512, 512)),
+                                         # exactly at the limit: ny * nz = 1048576 rows, so
+                                         # the last of the 16384 partial slots is used
+                                         ("f32", (1024, 1024, 8))])
 def test_matches_context_observe_on_two_calls(dtype, shape):
     import torch
 
@@ -40,7 +43,7 @@ def test_matches_context_observe_on_two_calls(dtype, shape):
     try:
         for call in range(2):
             if call == 0:
-                if len(shape) == 3 and shape[0] >= 256:
+                if shape == (512, 512, 512):
                     sim.init_sphere(r0=0.25)
                 else:
                     sim.load(wl.smooth_field(shape, seed=5))

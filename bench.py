@@ -200,6 +200,12 @@ def run_batch(args, ws, rank, local):
     """The batched workload: 512 uneven 2D grids, 2000 steps each, FP32,
     advanced by one persistent launch (graph-replayed) per job; compared
     with the same instances stepped one by one with ac_step."""
+    out = measure_batch(args, ws, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def measure_batch(args, ws, local):
     import numpy as np
     import torch
     import paper_2105_09671_gb300 as ac
@@ -213,8 +219,6 @@ def run_batch(args, ws, rank, local):
     cells = sum(d["n"] * d["n"] for d in inst)
     steps = inst[0]["steps"]
     b = ac.Batch(specs, dtype="f32", device=device, stream=stream)
-    if args.k:
-        b.set_schedule(abs(args.k))
     # initial states generated on the device by a Simulation view of each field
     views = []
     for i, d in enumerate(inst):
@@ -232,6 +236,13 @@ def run_batch(args, ws, rank, local):
             with torch.cuda.stream(stream):
                 b.phi(i).copy_(v.phi)
 
+    # depth: forced with --k, else autotuned on the batch's own fields
+    # (untimed; the fields are restored after every trial)
+    init_all()
+    if args.k:
+        b.set_schedule(abs(args.k))
+    else:
+        b.autotune(64)
     b.set_graph(True)
     n_vec = [steps] * len(inst)
     for _ in range(args.warmup):
@@ -276,7 +287,8 @@ def run_batch(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch512_2d", "instances": len(inst), "cells": cells,
                    "euler_steps_per_instance": steps, "sizes": "uniform {64,96,...,1024}^2",
-                   "eps": "uniform [3h, 6h]", "k": b.schedule(), "graph": True,
+                   "eps": "uniform [3h, 6h]", "k": b.schedule(), "k_choice": "forced" if args.k else "autotuned",
+                   "graph": True,
                    "l2": "no flush: 2 x %d MiB of fields exceed L2" % (cells * 4 >> 20)},
         "speedup_vs_plain": plain_ms / (total_ms / args.steps),
         "plain_per_instance_ms": plain_ms,
@@ -288,74 +300,185 @@ def run_batch(args, ws, rank, local):
     for v in views:
         v.close()
     b.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
-def run_learned(args, ws, rank, local):
-    """The learned form: train the 2D jump network on 256^2 plain trajectories
-    (eps = 4h), then advance a 1024^2 field 2000 steps (125 guarded jumps)
-    and compare time-to-solution and error with the plain stepper."""
+def measure_grid(w, dtype, jobs, warmup, local):
+    """Whole jobs (device initial state + w.steps graph-replayed steps) of
+    one workload grid on its default schedule: Gcell-updates/s and the mean
+    stencil launch time."""
+    import torch
+    import paper_2105_09671_gb300 as ac
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device)
+    sim = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype, device=device, stream=stream)
+    try:
+        sim.set_graph(True)
+        for _ in range(warmup):
+            init_field(sim, w)
+            sim.step(w.steps)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, launches = 0.0, 0
+        for _ in range(jobs):
+            init_field(sim, w)
+            c0 = sim.launch_count()
+            e0.record(stream)
+            sim.step(w.steps)
+            e1.record(stream)
+            stream.synchronize()
+            ms += e0.elapsed_time(e1)
+            launches += sim.launch_count() - c0
+        v, k = sim.schedule()
+        es = {"f64": 8, "f32": 4, "f16s": 2}[dtype]
+        peak, _ = hbm_peak()
+        launch_s = ms / 1e3 / max(1, launches)
+        return {"workload": w.name, "grid": list(w.shape), "dtype": dtype, "euler_steps": w.steps,
+                "jobs": jobs, "schedule": {"variant": "stream" if v == 2 else "direct", "k": k,
+                                           "tile": sim.tile()},
+                "value": w.cells * w.steps * jobs / (ms / 1e3) / 1e9, "unit": UNIT,
+                "avg_launch_ms": launch_s * 1e3,
+                "hbm_frac_per_launch": 2 * es * w.cells / launch_s / 1e9 / peak}
+    finally:
+        sim.close()
+
+
+def _learned_cases(args, net, ndim, n, jumps, guard, s, device):
+    """Guarded learned advance vs the plain FP32 stepper on an n^ndim grid
+    (eps = 4h) from a circle / sphere and from a random state; errors are
+    measured against the plain stepper run in FP64 on the GPU (the FP64
+    path the parity tests hold to the FP64 oracle within 1e-12)."""
     import numpy as np
     import torch
     import paper_2105_09671_gb300 as ac
     from paper_2105_09671_gb300 import _lib as L
 
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    s = torch.cuda.Stream(device)
-    net = L.ac_net_create(2, s.cuda_stream)
-    cfg = L.AcTrainConfig(n=256, eps_cells=4.0, pool=32, trajectory_jumps=125,
-                          iterations=args.train_iters, steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=1)
-    t0 = time.perf_counter()
-    hist, used = L.ac_net_train(net, cfg)
-    train_s = time.perf_counter() - t0
-    n, jumps = 1024, 125
+    shape = (n,) * ndim
     h = 1.0 / n
-    guard = L.AcGuard(16, 1e-6, 1.0 + 1e-3, 0.0)
+    eps, dt = 4 * h, 0.1 * h * h
+    steps = 16 * jumps
     out = {}
     for init in ("circle", "random"):
+        def start(sim):
+            if init == "circle":
+                sim.init_sphere(r0=0.3)
+            else:
+                sim.init_random(seed=7)
+        # the FP64 reference, from the FP32-rounded initial state (every torch
+        # operation on the library's stream s, which orders it with the steps)
+        ref32 = ac.Simulation(shape, h, eps, dt, dtype="f32", device=device, stream=s)
+        start(ref32)
+        ref64 = ac.Simulation(shape, h, eps, dt, dtype="f64", device=device, stream=s)
+        with torch.cuda.stream(s):
+            ref64.phi.copy_(ref32.phi.double())
+        ref64.step(steps)
+        with torch.cuda.stream(s):
+            ref = ref64.phi.clone()
+            ref_norm = float(torch.linalg.vector_norm(ref))
+        s.synchronize()
+        ref32.close()
+        ref64.close()
+        loose = L.AcGuard(guard.steps_per_jump, guard.energy_rtol, guard.max_abs, guard.residual_tol,
+                          guard.spot_rtol * math.sqrt(jumps), guard.spot_samples, guard.spot_size,
+                          guard.spot_seed)
         res = {}
-        for mode in ("plain", "learned"):
-            sim = ac.Simulation((n, n), h, 4 * h, 0.1 * h * h, dtype="f32", device=device, stream=s)
-            times = []
-            fb = 0
-            for rep in range(args.warmup + args.steps):
-                if init == "circle":
-                    sim.init_sphere(r0=0.3)
-                else:
-                    sim.init_random(seed=7)
+        for mode in ("plain", "learned", "learned_loose", "unguarded"):
+            sim = ac.Simulation(shape, h, eps, dt, dtype="f32", device=device, stream=s, pitch_x=n)
+            times, rep = [], None
+            reps = 1 if mode == "unguarded" else args.warmup + args.steps
+            for r in range(reps):
+                start(sim)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(s)
                 if mode == "learned":
-                    fb = L.ac_learned_advance(sim.ctx, net, jumps, guard)
+                    _, rep = L.ac_learned_advance(sim.ctx, net, jumps, guard, with_report=True)
+                elif mode == "learned_loose":
+                    _, rep = L.ac_learned_advance(sim.ctx, net, jumps, loose, with_report=True)
+                elif mode == "unguarded":
+                    _, rep = L.ac_learned_advance(sim.ctx, net, jumps, L.AcGuard(16, 1e30, 1e30, 0.0),
+                                                  with_report=True)
                 else:
-                    sim.step(16 * jumps)
+                    sim.step(steps)
                 e1.record(s)
                 s.synchronize()
-                if rep >= args.warmup:
+                if mode == "unguarded" or r >= args.warmup:
                     times.append(e0.elapsed_time(e1))
-            res[mode] = (statistics.median(times), fb, sim.to_numpy().astype(np.float64))
+            with torch.cuda.stream(s):
+                err = float(torch.linalg.vector_norm(sim.phi.double() - ref)) / ref_norm
+            s.synchronize()
+            res[mode] = (statistics.median(times), rep, err)
             sim.close()
-        ref = res["plain"][2]
-        out[init] = {"plain_ms": res["plain"][0], "learned_ms": res["learned"][0],
-                     "speedup_vs_plain": res["plain"][0] / res["learned"][0],
-                     "fallbacks": res["learned"][1], "jumps": jumps,
-                     "rel_l2_vs_plain_fp32": float(np.linalg.norm(res["learned"][2] - ref) / np.linalg.norm(ref))}
-    # tensor-core roofline of the network forward at 1024^2
-    x = torch.rand(1, n, n, device=device) * 2 - 1
+        lr, ll = res["learned"][1], res["learned_loose"][1]
+        out[init] = {
+            "plain_ms": res["plain"][0], "learned_ms": res["learned"][0],
+            "speedup_vs_plain": res["plain"][0] / res["learned"][0],
+            "jumps": jumps, "fallbacks": lr["fallbacks"],
+            "rejected": {k[9:]: lr[k] for k in lr if k.startswith("rejected_")},
+            "max_spot_rel": lr["max_spot_rel"], "max_residual": lr["max_residual"],
+            "rel_l2_vs_fp64": {"learned": res["learned"][2], "plain_fp32": res["plain"][2],
+                               "unguarded": res["unguarded"][2], "learned_loose": res["learned_loose"][2]},
+            "loose_guard": {"spot_rtol": loose.spot_rtol, "ms": res["learned_loose"][0],
+                            "fallbacks": ll["fallbacks"],
+                            "rejected": {k[9:]: ll[k] for k in ll if k.startswith("rejected_")}},
+            "unguarded_ms": res["unguarded"][0],
+        }
+    return out
+
+
+def run_learned(args, ws, rank, local):
+    """The learned form: train the 2D jump network on plain-stepper
+    trajectories of 256^2 grids (eps = 4h; 2000 trajectories by default),
+    calibrate its guard on held-out trajectories, then advance 1024^2
+    fields 2000 steps (125 guarded jumps) and compare time-to-solution and
+    error with the plain stepper; the same for the 3x3x3 network trained on
+    64^3 trajectories and evaluated on 128^3."""
+    import numpy as np
+    import torch
+    from paper_2105_09671_gb300 import _lib as L
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    s = torch.cuda.Stream(device)
+    jumps, target = 125, 1e-3
+
+    def train(ndim, n, pool, iterations, seed):
+        net = L.ac_net_create(ndim, s.cuda_stream)
+        cfg = L.AcTrainConfig(n=n, eps_cells=4.0, pool=pool, trajectory_jumps=jumps, iterations=iterations,
+                              steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=seed)
+        t0 = time.perf_counter()
+        hist, used = L.ac_net_train(net, cfg)
+        secs = time.perf_counter() - t0
+        # guard: the per-jump share of the final target for the spot check,
+        # the residual threshold calibrated on held-out trajectories
+        guard = L.AcGuard(16, 1e-6, 1.001, 0.0, target / jumps, 0, 0, 99)
+        cal = L.AcTrainConfig(n=n, eps_cells=4.0, pool=64 if ndim == 2 else 16, trajectory_jumps=jumps,
+                              iterations=1, steps_per_jump=16, lr=1e-3, lr_final=1e-5, seed=seed + 1000)
+        calib = L.ac_net_calibrate_guard(net, cal, 2.0, guard)
+        info = {"n": n, "pool": pool, "iterations": iterations, "trajectories": used, "seconds": secs,
+                "loss_first": float(np.median(hist[:50])), "loss_last": float(np.median(hist[-50:])),
+                "calibration": calib}
+        return net, guard, info
+
+    # 2D: enough iterations for the requested number of trajectories
+    pool2 = 32
+    iters2 = args.train_iters or int(math.ceil(max(0, args.train_trajectories - pool2) * jumps / pool2))
+    net2, guard2, train2 = train(2, 256, pool2, iters2, 1)
+    n2 = 1024
+    cases2 = _learned_cases(args, net2, 2, n2, jumps, guard2, s, device)
+    # tensor-core roofline of the 2D network forward at 1024^2
+    x = torch.rand(1, n2, n2, device=device) * 2 - 1
     y = torch.empty_like(x)
     torch.cuda.synchronize(device)
     for _ in range(3):
-        L.ac_net_forward(net, x.data_ptr(), y.data_ptr(), 1, n, n, 1, 0.1)
+        L.ac_net_forward(net2, x.data_ptr(), y.data_ptr(), 1, n2, n2, 1, 0.1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     for _ in range(10):
-        L.ac_net_forward(net, x.data_ptr(), y.data_ptr(), 1, n, n, 1, 0.1)
+        L.ac_net_forward(net2, x.data_ptr(), y.data_ptr(), 1, n2, n2, 1, 0.1)
     e1.record(s)
     s.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 10
-    flops = n * n * (4 * 2 * 288 * 32 + 2 * 2 * 9 * 32)
+    flops = n2 * n2 * (4 * 2 * 288 * 32 + 2 * 2 * 9 * 32)
     peak = 1889.1
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -363,24 +486,32 @@ def run_learned(args, ws, rank, local):
     except (OSError, KeyError, ValueError):
         pass
     achieved = flops / (fwd_ms / 1e3) / 1e12
-    cells_updates = n * n * 16 * jumps
+    guard_cfg = {k: getattr(guard2, k) for k, _ in guard2._fields_}
+    L.ac_net_destroy(net2)
+
+    out3 = None
+    if not args.no_3d:
+        net3, guard3, train3 = train(3, 64, 8, args.train3d_iters, 2)
+        cases3 = _learned_cases(args, net3, 3, 128, jumps, guard3, s, device)
+        L.ac_net_destroy(net3)
+        out3 = {"train": train3, "grid": [128] * 3, "cases": cases3}
+
+    c = cases2["circle"]
     line = {
-        "metric": METRIC, "value": cells_updates / (out["circle"]["learned_ms"] / 1e3) / 1e9, "unit": UNIT,
+        "metric": METRIC, "value": n2 * n2 * 16 * jumps / (c["learned_ms"] / 1e3) / 1e9, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": out["circle"]["learned_ms"], "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": c["learned_ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "learned_jump_1024_2d", "grid": [n, n], "euler_steps": 16 * jumps,
-                   "steps_per_jump": 16, "train": {"n": 256, "pool": 32, "iterations": args.train_iters,
-                                                   "trajectories": used, "seconds": train_s,
-                                                   "loss_first": float(np.median(hist[:50])),
-                                                   "loss_last": float(np.median(hist[-50:]))},
-                   "guard": {"energy_rtol": 1e-6, "max_abs": 1.001, "residual_tol": 0.0}},
-        "cases": out,
+        "config": {"workload": "learned_jump_1024_2d", "grid": [n2, n2], "euler_steps": 16 * jumps,
+                   "steps_per_jump": 16, "train": train2, "guard": guard_cfg,
+                   "target_rel_l2": target, "error_reference": "plain stepper in FP64 on the GPU"},
+        "cases": cases2,
+        "cases_3d": out3,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "network forward (4 tcgen05 convs + 2 CUDA-core end layers)",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "network forward (4 tcgen05 convs + 2 CUDA-core end layers)",
                      "forward_ms_1024": fwd_ms},
     }
-    L.ac_net_destroy(net)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -395,6 +526,19 @@ def run_reference(args, ws, rank):
     phi0 = (oracle.init_sphere(w.shape, w.h, w.r0, w.eps) if w.init == "sphere"
             else oracle.init_random(w.shape, seed=w.seed)).astype(np.float32).astype(np.float64)
     steps_per = args.ref_steps
+    if steps_per <= 0:
+        # each call pays a fixed set-up (allocating and filling the two
+        # ghost-extended FP64 fields) before its steps: size the steps per
+        # benchmark step from a 1-step and a 5-step timing so that a call
+        # takes about --ref-seconds and the set-up is a small share of it
+        t0 = time.perf_counter()
+        oracle.step(phi0, w.h, w.eps, w.dt, 1)
+        t1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.step(phi0, w.h, w.eps, w.dt, 5)
+        t5 = time.perf_counter() - t0
+        per_step = max((t5 - t1) / 4.0, t5 / 20.0, 1e-9)
+        steps_per = int(max(1, min(w.steps, args.ref_seconds / per_step)))
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -489,10 +633,34 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public API with host buffers: every job copies
     # its initial state from pinned host memory (H2D), runs the steps and
-    # copies the final field back (D2H).  Two simulations alternate so that
-    # job i+1's H2D and job i's D2H overlap the stepping of the other job
-    # (separate copy streams, ordered by events); every copy is inside the
-    # timed region.
+    # copies the final field back (D2H), all inside the timed region.
+    # (1) one job at a time on one stream: copy in, step, copy out.
+    host_in = torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True)
+    host_out = [torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True) for _ in range(2)]
+    init_field(sim, w)
+    with torch.cuda.stream(stream):
+        host_in.copy_(sim.phi, non_blocking=True)
+    stream.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    dist_barrier(ws, device)
+    torch.cuda.synchronize(device)
+    s_s, s_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_s.record(stream)
+    for i in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            sim.phi.copy_(host_in, non_blocking=True)
+        sim.step(w.steps)
+        with torch.cuda.stream(stream):
+            host_out[0].copy_(sim.phi, non_blocking=True)
+    s_e.record(stream)
+    torch.cuda.synchronize(device)
+    single_ms = dist_max(ws, s_s.elapsed_time(s_e), device)
+    single_value = w.cells * w.steps * e2e_steps * ws / (single_ms / 1e3) / 1e9
+    if not torch.isfinite(host_out[0]).all():
+        raise RuntimeError("end-to-end job produced a non-finite field")
+    # (2) pipelined: two simulations alternate so that job i+1's H2D and job
+    # i's D2H overlap the stepping of the other job (separate copy streams,
+    # ordered by events); the two jobs' stepping may overlap on the GPU too.
     sim2 = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype, device=device,
                          stream=torch.cuda.Stream(device))
     if args.k:
@@ -501,14 +669,7 @@ def run_ours(args, ws, rank, local):
     sim2.step(w.steps)  # captures its graph outside the timed region
     sim2.stream.synchronize()
     sims = (sim, sim2)
-    host_in = torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True)
-    host_out = [torch.empty(w.shape, dtype=sim.phi.dtype, pin_memory=True) for _ in range(2)]
-    init_field(sim, w)
-    with torch.cuda.stream(stream):
-        host_in.copy_(sim.phi, non_blocking=True)
-    stream.synchronize()
     copy_in, copy_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
-    e2e_steps = max(1, min(args.steps, 3))
     dist_barrier(ws, device)
     torch.cuda.synchronize(device)
     e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,13 +717,36 @@ def run_ours(args, ws, rank, local):
                      "kernel": kid, "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                      "effective_frac_k1": value / ws * 2 * es / peak},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
-                "d2h_bytes_per_step": field_bytes},
+        "e2e": {"value": single_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
+                "d2h_bytes_per_step": field_bytes, "jobs": e2e_steps,
+                "how": "one job at a time on one stream: H2D of the initial field from pinned "
+                       "memory, the Euler steps, D2H of the final field"},
+        "e2e_pipelined": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
+                          "d2h_bytes_per_step": field_bytes, "jobs": e2e_steps,
+                          "how": "two simulations alternate; copies on copy streams overlap the "
+                                 "other job's stepping"},
         "gpu_launches": launches,
         "clocks": clk,
         "result": {"energy": obs[0], "phase_volume": obs[1], "nonfinite": obs[2],
                    "radius": ((3 * obs[1]) / (4 * math.pi)) ** (1 / 3) if w.ndim == 3 else math.sqrt(obs[1] / math.pi)},
     }
+    if ws == 1 and not args.no_secondary:
+        # the other workloads, timed here as well so that their figures come
+        # from the same run (each guarded: a failure is reported, not raised)
+        from paper_2105_09671_gb300 import workloads as wl
+        sec = {}
+        for name, fn in (("separation4096_f32", lambda: measure_grid(wl.SEPARATION_4096, "f32", 3, 3, local)),
+                         ("sphere512_f16s", lambda: measure_grid(w, "f16s", 3, 3, local) if w.name == "sphere3d_512"
+                          else None),
+                         ("batch512", lambda: measure_batch(argparse.Namespace(steps=2, warmup=3, k=0), 1, local))):
+            try:
+                r = fn()
+                if r is not None:
+                    sec[name] = {k2: r[k2] for k2 in r if k2 not in ("metric", "clocks", "roofline")} \
+                        if name == "batch512" else r
+            except Exception as e:  # noqa: BLE001 - reported in the JSON line
+                sec[name] = {"error": f"{type(e).__name__}: {e}"}
+        out["secondary"] = sec
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         steps, secs, cores = oracle_sample(w, args.cpu_seconds)
         out["cpu_baseline"] = {
@@ -591,12 +775,20 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sphere512",
                     choices=["sphere512", "separation4096", "batch512", "learned1024"])
-    ap.add_argument("--train-iters", type=int, default=1500)
+    ap.add_argument("--train-iters", type=int, default=0,
+                    help="learned workload: Adam steps of the 2D network (0: from --train-trajectories)")
+    ap.add_argument("--train-trajectories", type=int, default=2000)
+    ap.add_argument("--train3d-iters", type=int, default=1500)
+    ap.add_argument("--no-3d", action="store_true", help="learned workload: skip the 3D network")
     ap.add_argument("--k", type=int, default=0,
                     help="force the temporal-block depth (negative: direct kernel, k=1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched / 4096^2 / FP16-storage figures of the default run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-steps", type=int, default=4)
+    ap.add_argument("--ref-steps", type=int, default=0,
+                    help="oracle steps per benchmark step of --impl reference (0: sized to --ref-seconds)")
+    ap.add_argument("--ref-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

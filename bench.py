@@ -137,9 +137,9 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel: str, source: str):
+def recorded_traffic(kernel: str, source: str, grid=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current kernel source and on this grid (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
@@ -148,6 +148,8 @@ def recorded_traffic(kernel: str, source: str):
     except (OSError, ValueError, AttributeError):
         return None
     if not rec or rec.get("source_sha256") != sha:
+        return None
+    if grid is not None and rec.get("grid") != list(grid):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -287,7 +289,8 @@ def measure_batch(args, ws, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch512_2d", "instances": len(inst), "cells": cells,
                    "euler_steps_per_instance": steps, "sizes": "uniform {64,96,...,1024}^2",
-                   "eps": "uniform [3h, 6h]", "k": b.schedule(), "k_choice": "forced" if args.k else "autotuned",
+                   "eps": "uniform [3h, 6h]", "k": b.schedule(), "tile": b.tile(),
+                   "k_choice": "forced" if args.k else "autotuned",
                    "graph": True,
                    "l2": "no flush: 2 x %d MiB of fields exceed L2" % (cells * 4 >> 20)},
         "speedup_vs_plain": plain_ms / (total_ms / args.steps),
@@ -580,7 +583,7 @@ def run_ours(args, ws, rank, local):
     sim.set_graph(True)
     variant, k = sim.schedule()
     tile = sim.tile()
-    kid = f"{kname} k={k}" + (f" tile={tile}" if len(w.shape) == 3 else "")
+    kid = f"{kname} k={k} tile={tile}"
     es = {"f64": 8, "f32": 4, "f16s": 2}[dtype]
     field_bytes = w.cells * es
 
@@ -629,7 +632,7 @@ def run_ours(args, ws, rank, local):
     alg_bytes = 2 * field_bytes
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic = recorded_traffic(kid, ksrc) if variant == ac.AC_VARIANT_STREAM else None
+    traffic = recorded_traffic(kid, ksrc, w.shape) if variant == ac.AC_VARIANT_STREAM else None
 
     # end to end through the public API with host buffers: every job copies
     # its initial state from pinned host memory (H2D), runs the steps and

@@ -447,14 +447,22 @@ int ac_batch_create(const ac_grid_desc *descs, void *const *phi_devs, int32_t co
  * Re-planning (new n values or k) synchronises the stream once. */
 int ac_batch_step(ac_batch *batch, const int64_t *n_per_instance);
 
-/* Temporal-block depth k (1..4) of every instance; 0 = default (4 for
- * FP32/FP16 storage, 1 for FP64). */
+/* Temporal-block depth k of every instance: 1..4 with tile 0, 1..6 with
+ * tile 1; 0 = default (4 for FP32/FP16 storage, 1 for FP64). */
 int ac_batch_set_schedule(ac_batch *batch, int32_t k);
 int ac_batch_get_schedule(ac_batch *batch, int32_t *k);
 
-/* Time k = 1..4 on the batch's own fields (steps_per_trial steps each,
- * fields saved to a temporary device buffer this call allocates and
- * restored after each trial) and keep the fastest.  Synchronises. */
+/* Strip width of every instance's work items (as the 2D tiles of
+ * ac_set_tile): 0 = the storage type's default strips, 1 = FP32 strips of
+ * 8 cells per lane (AC_ERR_UNSUPPORTED for other storage types, or while
+ * the depth exceeds what the tile offers).  Results do not depend on it. */
+int ac_batch_set_tile(ac_batch *batch, int32_t tile);
+int ac_batch_get_tile(ac_batch *batch, int32_t *tile);
+
+/* Time every (tile, k) the storage type offers on the batch's own fields
+ * (steps_per_trial steps each, fields saved to a temporary device buffer
+ * this call allocates and restored after each trial) and keep the fastest.
+ * Synchronises. */
 int ac_batch_autotune(ac_batch *batch, int64_t steps_per_trial);
 
 /* Replay ac_batch_step through a CUDA graph (captured on the first call per
@@ -511,8 +519,8 @@ int ac_slab_plan(int64_t extent, int32_t parts, int32_t halo, ac_slab_part *out)
 /* In-process slabs on the current device: `parts` contexts over extended
  * slabs that this call allocates (field and workspace each; freed by
  * ac_slab_destroy), all on cuda_stream.  halo = 0 takes twice the default
- * temporal-block depth of the grid kind and storage type (3D: 4; 2D: 12
- * for FP32, 8 for FP16 storage; FP64: 2), so that a block is two passes.  Halo exchanges are device-to-device copies of contiguous
+ * temporal-block depth of the grid (3D: 4; 2D: 8, or 12 for FP32 grids of
+ * at least 1024^2 cells; FP64: 2), so that a block is two passes.  Halo exchanges are device-to-device copies of contiguous
  * plane blocks on the stream. */
 typedef struct ac_slab ac_slab; /* opaque */
 int ac_slab_create(const ac_grid_desc *desc, int32_t parts, int32_t halo, void *cuda_stream,

@@ -33,7 +33,7 @@ EXPORTED = (
     "ac_set_graph", "ac_status", "ac_launch_count", "ac_observe_noalloc", "ac_destroy",
     "ac_last_error", "ac_version",
     "ac_batch_workspace_bytes", "ac_batch_create", "ac_batch_step", "ac_batch_set_schedule",
-    "ac_batch_get_schedule", "ac_batch_autotune", "ac_batch_set_graph", "ac_batch_observe",
+    "ac_batch_get_schedule", "ac_batch_set_tile", "ac_batch_get_tile", "ac_batch_autotune", "ac_batch_set_graph", "ac_batch_observe",
     "ac_batch_status", "ac_batch_set_wait_limit", "ac_batch_launch_count", "ac_batch_destroy",
     "ac_tc_gemm_bf16_n32",
     "ac_net_param_count", "ac_net_create", "ac_net_set_params", "ac_net_get_params",
@@ -182,6 +182,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_batch_step": [vp, ctypes.POINTER(i64)],
         "ac_batch_set_schedule": [vp, i32],
         "ac_batch_get_schedule": [vp, ctypes.POINTER(i32)],
+        "ac_batch_set_tile": [vp, i32],
+        "ac_batch_get_tile": [vp, ctypes.POINTER(i32)],
         "ac_batch_autotune": [vp, i64],
         "ac_batch_set_graph": [vp, i32],
         "ac_batch_observe": [vp, i32, ctypes.POINTER(dbl)],
@@ -387,6 +389,16 @@ def ac_batch_step(batch: int, n_per_instance) -> None:
 
 def ac_batch_set_schedule(batch: int, k: int) -> None:
     check(lib().ac_batch_set_schedule(ctypes.c_void_p(batch), int(k)))
+
+
+def ac_batch_set_tile(batch: int, tile: int) -> None:
+    check(lib().ac_batch_set_tile(ctypes.c_void_p(batch), int(tile)))
+
+
+def ac_batch_get_tile(batch: int) -> int:
+    t = ctypes.c_int32()
+    check(lib().ac_batch_get_tile(ctypes.c_void_p(batch), ctypes.byref(t)))
+    return t.value
 
 
 def ac_batch_get_schedule(batch: int) -> int:

@@ -252,19 +252,32 @@ static bool schedule_ok(const ac_ctx *c, int variant, int k, int tile = 0) {
   return false;
 }
 
-int ac_default_depth(int ndim, int dtype) {
+// 2D FP32 grids from this many cells on take the 8-cell strips by default:
+// measured on GB300, 4096^2 at k = 6 with 8-cell strips runs at 1634
+// Gcell-updates/s against 1485 for 4-cell strips at k = 4, 8192^2 at 2006
+// against 1841; grids of a few hundred cells per side, which are bound by
+// launch latency and leave most lanes of a 240-column strip idle, keep the
+// 4-cell strips (512 grids of 64^2 .. 1024^2 stepped one by one: 3.2 s
+// against 4.5 s with the wide strips).
+constexpr double kWideStripCells = 1024.0 * 1024.0;
+
+static bool wide_default(const ac_grid_desc *d) {
+  return d->ndim == 2 && d->dtype == AC_F32 && (double)d->nx * (double)d->ny >= kWideStripCells;
+}
+
+int ac_default_depth(const ac_grid_desc *d) {
   // FP64 is bound by the GPU's FP64 rate, where the redundant halo work of
   // temporal blocking costs more than the memory traffic it saves: one step
   // per launch.  FP32 / FP16 storage stream with k > 1 (measured best on
-  // GB300: 3D k = 2; 2D FP32 k = 6 with 8-cell strips, FP16 storage k = 4).
-  if (dtype == AC_F64) return 1;
-  if (ndim == 3) return 2;
-  return dtype == AC_F32 ? 6 : 4;
+  // GB300: 3D k = 2; 2D k = 4, or 6 with the 8-cell FP32 strips).
+  if (d->dtype == AC_F64) return 1;
+  if (d->ndim == 3) return 2;
+  return wide_default(d) ? 6 : 4;
 }
 
 static void default_schedule(const ac_ctx *c, int *variant, int *k) {
   *variant = c->d.dtype == AC_F64 ? AC_VARIANT_DIRECT : AC_VARIANT_STREAM;
-  *k = ac_default_depth(c->d.ndim, c->d.dtype);
+  *k = ac_default_depth(&c->d);
   if (*variant == AC_VARIANT_STREAM && !schedule_ok(c, *variant, *k, 0) &&
       !schedule_ok(c, *variant, *k, 1))
     *k = 1;
@@ -281,10 +294,9 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
 // k <= 2 (FP16 storage at k = 1: several CTAs per SM, tile 1); k = 3 needs
 // the register room of four rows per thread with half the threads (tile 2).
 static int default_tile(const ac_ctx *c, int k) {
-  // 2D FP32: strips of 8 cells per lane wherever they are offered (k <= 6;
-  // 4096^2 at k = 6: 1634 against 1485 Gcell-updates/s for 4-cell strips at
-  // k = 4, 8192^2: 2006 against 1841)
-  if (c->d.ndim == 2) return c->d.dtype == AC_F32 && k <= 6 ? 1 : 0;
+  // 2D FP32 grids from 1024^2 cells on: strips of 8 cells per lane wherever
+  // they are offered (k <= 6; see kWideStripCells)
+  if (c->d.ndim == 2) return wide_default(&c->d) && k <= 6 ? 1 : 0;
   if (c->d.dtype == AC_F64) return k == 1 ? 0 : 2;
   if (c->d.dtype == AC_F16S) return k == 1 ? 1 : 0;
   return k == 3 ? 2 : 0;

@@ -44,9 +44,10 @@ struct ac_batch {
   std::vector<ac_grid_desc> d;
   std::vector<void *> phi, ws;
   int k = 0;            // plan depth (0 = default)
+  int tile = 0;         // strip width (0: default strips, 1: 8-cell FP32 strips)
   int chunk_rows = 64;  // rows per work item
   bool items_valid = false;
-  int items_k = -1;
+  int items_k = -1, items_tile = -1;
   // host / device tables
   std::vector<BInst> h_inst;
   std::vector<BItem> h_items;
@@ -54,7 +55,8 @@ struct ac_batch {
   std::vector<int> odd;  // instances whose plan ends in the workspace
   BInst *d_inst = nullptr;
   BItem *d_items = nullptr;
-  CUtensorMap *d_maps = nullptr;
+  CUtensorMap *d_maps = nullptr;       // [instance][phi, ws], box of tile-0 strips
+  CUtensorMap *d_maps_wide = nullptr;  // the same for tile-1 strips (FP32 only)
   int *d_progress = nullptr;
   unsigned long long *d_ticket = nullptr;
   int *d_status = nullptr;
@@ -86,11 +88,11 @@ static void release_graph(ac_batch *b) {
 // Work items for plan depth k: per instance, strips of the 2D streaming
 // kernel (halo HX(k)) times row chunks, each with its 3 x 3 neighbourhood.
 static int build_items(ac_batch *b, int k) {
-  if (b->items_valid && b->items_k == k) return AC_OK;
+  if (b->items_valid && b->items_k == k && b->items_tile == b->tile) return AC_OK;
   release_items(b);
   release_graph(b);
   int sw, hx, ow, vec;
-  batch_strip_geom(b->dtype, k, &sw, &hx, &ow, &vec);
+  batch_strip_geom(b->dtype, k, b->tile, &sw, &hx, &ow, &vec);
   b->h_items.clear();
   for (int i = 0; i < b->count; ++i) {
     const ac_grid_desc &d = b->d[i];
@@ -121,6 +123,7 @@ static int build_items(ac_batch *b, int k) {
   BC_CUDA(cudaMalloc(&b->d_progress, sizeof(int) * b->h_items.size()));
   b->items_valid = true;
   b->items_k = k;
+  b->items_tile = b->tile;
   return AC_OK;
 }
 
@@ -183,31 +186,38 @@ extern "C" int ac_batch_create(const ac_grid_desc *descs, void *const *phi_devs,
     in.beta = descs[i].dt / (descs[i].h * descs[i].h);
   }
   // per-instance tensor maps of phi and workspace (box SW x rows, zero fill)
-  // over-aligned type: a plain 64-byte aligned host array
+  // for each strip width the storage type offers; over-aligned type: a
+  // plain 64-byte aligned host array
+  const int n_tiles = batch_kmax(b->dtype, 1) > 0 ? 2 : 1;
   const size_t n_maps = 2 * (size_t)count;
   CUtensorMap *maps = static_cast<CUtensorMap *>(
-      std::aligned_alloc(64, (sizeof(CUtensorMap) * n_maps + 63) / 64 * 64));
+      std::aligned_alloc(64, (sizeof(CUtensorMap) * n_maps * n_tiles + 63) / 64 * 64));
   if (!maps) { delete b; return bfail(AC_ERR_NOMEM, "out of host memory"); }
   EncodeTiledFn fn = ac_encode_fn();
-  int sw, hx, ow, vec;
-  batch_strip_geom(b->dtype, 1, &sw, &hx, &ow, &vec);
   const size_t es = ac_elem_size(b->dtype);
   int rc = AC_OK;
   if (!fn) rc = bfail(AC_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
-  for (int i = 0; i < count && rc == AC_OK; ++i)
-    for (int w = 0; w < 2 && rc == AC_OK; ++w) {
-      cuuint64_t dims[2] = {(cuuint64_t)descs[i].nx, (cuuint64_t)descs[i].ny};
-      cuuint64_t strides[1] = {(cuuint64_t)(descs[i].pitch_x * es)};
-      cuuint32_t box[2] = {(cuuint32_t)sw, (cuuint32_t)kBatchBoxRows}, estr[2] = {1, 1};
-      CUresult r = fn(&maps[2 * i + w], ac_tmap_type(b->dtype), 2, w ? b->ws[i] : b->phi[i], dims,
-                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) rc = bfail(AC_ERR_CUDA, "instance %d: tensor map encode failed (%d)", i, (int)r);
-    }
+  for (int t = 0; t < n_tiles && rc == AC_OK; ++t) {
+    int sw, hx, ow, vec;
+    batch_strip_geom(b->dtype, 1, t, &sw, &hx, &ow, &vec);
+    for (int i = 0; i < count && rc == AC_OK; ++i)
+      for (int w = 0; w < 2 && rc == AC_OK; ++w) {
+        cuuint64_t dims[2] = {(cuuint64_t)descs[i].nx, (cuuint64_t)descs[i].ny};
+        cuuint64_t strides[1] = {(cuuint64_t)(descs[i].pitch_x * es)};
+        cuuint32_t box[2] = {(cuuint32_t)sw, (cuuint32_t)kBatchBoxRows}, estr[2] = {1, 1};
+        CUresult r = fn(&maps[t * n_maps + 2 * i + w], ac_tmap_type(b->dtype), 2, w ? b->ws[i] : b->phi[i],
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) rc = bfail(AC_ERR_CUDA, "instance %d: tensor map encode failed (%d)", i, (int)r);
+      }
+  }
   cudaError_t e = cudaSuccess;
   if (rc == AC_OK) {
     e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * n_maps);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_maps, maps, sizeof(CUtensorMap) * n_maps, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_tiles > 1) e = cudaMalloc(&b->d_maps_wide, sizeof(CUtensorMap) * n_maps);
+    if (e == cudaSuccess && n_tiles > 1)
+      e = cudaMemcpy(b->d_maps_wide, maps + n_maps, sizeof(CUtensorMap) * n_maps, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, sizeof(BInst) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
@@ -220,7 +230,7 @@ extern "C" int ac_batch_create(const ac_grid_desc *descs, void *const *phi_devs,
   std::free(maps);
   if (rc != AC_OK) {
     cudaGetLastError();
-    cudaFree(b->d_maps); cudaFree(b->d_inst); cudaFree(b->d_ticket); cudaFree(b->d_status);
+    cudaFree(b->d_maps); cudaFree(b->d_maps_wide); cudaFree(b->d_inst); cudaFree(b->d_ticket); cudaFree(b->d_status);
     cudaFree(b->d_partials); cudaFree(b->d_out); cudaFreeHost(b->h_out);
     delete b;
     return rc;
@@ -234,7 +244,7 @@ extern "C" int ac_batch_destroy(ac_batch *b) {
   cudaStreamSynchronize(b->stream);
   release_graph(b);
   release_items(b);
-  cudaFree(b->d_maps); cudaFree(b->d_inst); cudaFree(b->d_ticket); cudaFree(b->d_status);
+  cudaFree(b->d_maps); cudaFree(b->d_maps_wide); cudaFree(b->d_inst); cudaFree(b->d_ticket); cudaFree(b->d_status);
   cudaFree(b->d_partials); cudaFree(b->d_out); cudaFreeHost(b->h_out);
   delete b;
   return AC_OK;
@@ -242,10 +252,31 @@ extern "C" int ac_batch_destroy(ac_batch *b) {
 
 extern "C" int ac_batch_set_schedule(ac_batch *b, int32_t k) {
   if (!b) return bfail(AC_ERR_INVALID, "batch is NULL");
-  if (k < 0 || k > kBatchKMax) return bfail(AC_ERR_INVALID, "k must be in 0..%d (0 = default)", kBatchKMax);
+  const int kmax = batch_kmax(b->dtype, b->tile);
+  if (k < 0 || k > kmax)
+    return bfail(AC_ERR_INVALID, "k must be in 0..%d (0 = default) for tile %d", kmax, b->tile);
   if (k != b->k) release_graph(b);
   b->k = k;
   b->cur_n.clear();
+  return AC_OK;
+}
+
+extern "C" int ac_batch_set_tile(ac_batch *b, int32_t tile) {
+  if (!b) return bfail(AC_ERR_INVALID, "batch is NULL");
+  if (tile < 0 || tile > 1) return bfail(AC_ERR_INVALID, "tile must be 0 or 1");
+  if (batch_kmax(b->dtype, tile) == 0)
+    return bfail(AC_ERR_UNSUPPORTED, "tile %d is offered for FP32 storage only", tile);
+  if (b->k > batch_kmax(b->dtype, tile))
+    return bfail(AC_ERR_UNSUPPORTED, "depth %d is not offered with tile %d", b->k, tile);
+  if (tile != b->tile) release_graph(b);
+  b->tile = tile;
+  b->cur_n.clear();
+  return AC_OK;
+}
+
+extern "C" int ac_batch_get_tile(ac_batch *b, int32_t *tile) {
+  if (!b || !tile) return bfail(AC_ERR_INVALID, "NULL argument");
+  *tile = b->tile;
   return AC_OK;
 }
 
@@ -288,8 +319,9 @@ static int enqueue(ac_batch *b) {
   BC_CUDA(cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned long long), b->stream));
   int grid = 0;
   if (b->total_tickets > 0) {
-    cudaError_t e = batch2d_launch(b->dtype, b->d_inst, b->d_items, (int)b->h_items.size(),
-                                   b->d_maps, b->d_progress, b->d_ticket, b->total_tickets,
+    cudaError_t e = batch2d_launch(b->dtype, b->tile, b->d_inst, b->d_items, (int)b->h_items.size(),
+                                   b->tile ? b->d_maps_wide : b->d_maps, b->d_progress, b->d_ticket,
+                                   b->total_tickets,
                                    b->d_status, b->wait_limit, b->num_sms, b->stream, &grid);
     if (e != cudaSuccess) return bfail(AC_ERR_CUDA, "batched launch failed: %s", cudaGetErrorString(e));
     ++b->launches;
@@ -408,14 +440,19 @@ extern "C" int ac_batch_autotune(ac_batch *b, int64_t steps_per_trial) {
   }
   const bool graph_was = b->use_graph;
   b->use_graph = false;
-  const int k_was = b->k;
+  const int k_was = b->k, tile_was = b->tile;
   std::vector<int64_t> n(b->count, steps_per_trial);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best_k = default_k(b->dtype), rc = AC_OK;
+  int best_k = default_k(b->dtype), best_tile = 0, rc = AC_OK;
   float best = 1e30f;
-  for (int k = 1; k <= kBatchKMax && rc == AC_OK; ++k) {
+  std::vector<std::pair<int, int>> cand;  // (tile, k)
+  for (int t = 0; t < 2; ++t)
+    for (int k = 1; k <= batch_kmax(b->dtype, t); ++k) cand.push_back({t, k});
+  for (size_t ci = 0; ci < cand.size() && rc == AC_OK; ++ci) {
+    const int k = cand[ci].second;
+    b->tile = cand[ci].first;
     b->k = k;
     b->cur_n.clear();
     rc = ac_batch_step(b, n.data());  // warm-up (builds items, plans)
@@ -426,7 +463,7 @@ extern "C" int ac_batch_autotune(ac_batch *b, int64_t steps_per_trial) {
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_k = k; }
+    if (ms < best) { best = ms; best_k = k; best_tile = b->tile; }
     for (int i = 0; i < b->count; ++i)
       cudaMemcpyAsync(b->phi[i], backup + offs[i], bfield_bytes(b->d[i]), cudaMemcpyDeviceToDevice, b->stream);
   }
@@ -436,19 +473,24 @@ extern "C" int ac_batch_autotune(ac_batch *b, int64_t steps_per_trial) {
   cudaFree(backup);
   b->use_graph = graph_was;
   b->k = rc == AC_OK ? best_k : k_was;
+  b->tile = rc == AC_OK ? best_tile : tile_was;
   b->cur_n.clear();
   release_graph(b);
   return rc;
 }
 
 namespace ac {
-cudaError_t batch2d_launch(int dtype, const BInst *insts, const BItem *items, int n_items,
+cudaError_t batch2d_launch(int dtype, int tile, const BInst *insts, const BItem *items, int n_items,
                            const CUtensorMap *maps, int *progress, unsigned long long *ticket,
                            long long total, int *status, uint32_t wait_limit, int num_sms,
                            cudaStream_t s, int *grid_out) {
+  if (batch_kmax(dtype, tile) == 0) return cudaErrorInvalidValue;
   switch (dtype) {
     case AC_F64: return batch2d_launch_f64(insts, items, n_items, maps, progress, ticket, total, status, wait_limit, num_sms, s, grid_out);
-    case AC_F32: return batch2d_launch_f32(insts, items, n_items, maps, progress, ticket, total, status, wait_limit, num_sms, s, grid_out);
+    case AC_F32:
+      if (tile == 1)
+        return batch2d_launch_f32_wide(insts, items, n_items, maps, progress, ticket, total, status, wait_limit, num_sms, s, grid_out);
+      return batch2d_launch_f32(insts, items, n_items, maps, progress, ticket, total, status, wait_limit, num_sms, s, grid_out);
     case AC_F16S: return batch2d_launch_f16(insts, items, n_items, maps, progress, ticket, total, status, wait_limit, num_sms, s, grid_out);
   }
   return cudaErrorInvalidValue;

@@ -77,7 +77,7 @@ extern "C" int ac_slab_create(const ac_grid_desc *desc, int32_t parts, int32_t h
   if (rc) return rc;
   const bool d3 = desc->ndim == 3;
   const int64_t extent = d3 ? desc->nz : desc->ny;
-  if (halo == 0) halo = 2 * ac_default_depth(desc->ndim, desc->dtype);  // two full passes per block
+  if (halo == 0) halo = 2 * ac_default_depth(desc);  // two full passes per block
   std::vector<ac_slab_part> plan(parts > 0 ? parts : 1);
   rc = ac_slab_plan(extent, parts, halo, plan.data());
   if (rc) return rc;

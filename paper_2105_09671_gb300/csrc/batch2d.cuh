@@ -48,16 +48,18 @@ __device__ __forceinline__ bool wait_at_least(const int *p, int target, uint32_t
   return false;
 }
 
-template <typename T, int D>
+template <typename T, int D, int VPL>
 __device__ __forceinline__ bool batch_item(const S2Ring<T> &ring, uint32_t &u, const CUtensorMap *map,
                                            T *dst, const S2Item &si, const BInst &in, int *status) {
   using C = typename Traits<T>::C;
   if (in.fastx)
-    return s2_item<T, D, true>(ring.smem, ring.bars, u, map, dst, si, (C)in.alpha, (C)in.beta, status);
-  return s2_item<T, D, false>(ring.smem, ring.bars, u, map, dst, si, (C)in.alpha, (C)in.beta, status);
+    return s2_item<T, D, true, VPL>(ring.smem, ring.bars, u, map, dst, si, (C)in.alpha, (C)in.beta, status);
+  return s2_item<T, D, false, VPL>(ring.smem, ring.bars, u, map, dst, si, (C)in.alpha, (C)in.beta, status);
 }
 
-template <typename T>
+// VPL: 16-byte vectors per lane of every strip (the storage type's default,
+// or 2 for the 8-cell FP32 strips, depths up to kBatchKMaxWide).
+template <typename T, int VPL>
 __global__ void __launch_bounds__(kS2Warps * 32, 1)
     batch2d_k(const BInst *__restrict__ insts, const BItem *__restrict__ items, int n_items,
               const CUtensorMap *__restrict__ maps, int *progress,
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
               uint32_t wait_limit) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const S2Ring<T> ring = s2_ring<T, 1>(smem, warp);  // ring size depends on T only
+  const S2Ring<T> ring = s2_ring<T, 1, VPL>(smem, warp);  // ring size depends on T and VPL only
   if (lane == 0) {
     for (int s = 0; s < kS2Stages; ++s) mbar_init(&ring.bars[s], 1);
     fence_mbar_init();
@@ -114,12 +116,21 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
     si.nx = in.nx;
     si.ny = in.ny;
     si.pitch = in.pitch;
+    constexpr bool WIDE = VPL != S2Cfg<T>::VPL;
     bool ok = false;
     switch (d) {
-      case 1: ok = batch_item<T, 1>(ring, u, map, dst, si, in, status); break;
-      case 2: ok = batch_item<T, 2>(ring, u, map, dst, si, in, status); break;
-      case 3: ok = batch_item<T, 3>(ring, u, map, dst, si, in, status); break;
-      case 4: ok = batch_item<T, 4>(ring, u, map, dst, si, in, status); break;
+      case 1: ok = batch_item<T, 1, VPL>(ring, u, map, dst, si, in, status); break;
+      case 2: ok = batch_item<T, 2, VPL>(ring, u, map, dst, si, in, status); break;
+      case 3: ok = batch_item<T, 3, VPL>(ring, u, map, dst, si, in, status); break;
+      case 4: ok = batch_item<T, 4, VPL>(ring, u, map, dst, si, in, status); break;
+      case 5:
+        if constexpr (WIDE) { ok = batch_item<T, 5, VPL>(ring, u, map, dst, si, in, status); break; }
+        if (lane == 0) atomicExch(status, AC_ERR_INVALID);
+        return;
+      case 6:
+        if constexpr (WIDE) { ok = batch_item<T, 6, VPL>(ring, u, map, dst, si, in, status); break; }
+        if (lane == 0) atomicExch(status, AC_ERR_INVALID);
+        return;
       default: if (lane == 0) atomicExch(status, AC_ERR_INVALID); return;
     }
     if (!ok) return;
@@ -129,26 +140,27 @@ __global__ void __launch_bounds__(kS2Warps * 32, 1)
   }
 }
 
-template <typename T>
+template <typename T, int VPL>
 struct BatchGeom {
-  static constexpr int SW = S2Geom<T, 1>::SW;
+  static constexpr int SW = S2Geom<T, 1, VPL>::SW;
   static constexpr int V = Traits<T>::V;
-  static constexpr int SMEM = S2Geom<T, 1>::SMEM;
+  static constexpr int SMEM = S2Geom<T, 1, VPL>::SMEM;
 };
 
-template <typename T>
+template <typename T, int VPL = S2Cfg<T>::VPL>
 cudaError_t batch2d_launch_t(const BInst *insts, const BItem *items, int n_items,
                              const CUtensorMap *maps, int *progress,
                              unsigned long long *ticket, long long total, int *status,
                              uint32_t wait_limit, int num_sms, cudaStream_t s, int *grid_out) {
   static KernelSetup ks;
   int occ = 1;
-  cudaError_t e = kernel_setup(ks, (const void *)batch2d_k<T>, kS2Warps * 32, BatchGeom<T>::SMEM, &occ);
+  cudaError_t e = kernel_setup(ks, (const void *)batch2d_k<T, VPL>, kS2Warps * 32,
+                               BatchGeom<T, VPL>::SMEM, &occ);
   if (e != cudaSuccess) return e;
   // every CTA of the grid must be resident at once (the waits rely on it)
   const int blocks = std::max(1, num_sms) * occ;
   if (grid_out) *grid_out = blocks;
-  batch2d_k<T><<<blocks, kS2Warps * 32, BatchGeom<T>::SMEM, s>>>(
+  batch2d_k<T, VPL><<<blocks, kS2Warps * 32, BatchGeom<T, VPL>::SMEM, s>>>(
       insts, items, n_items, maps, progress, ticket, total, status, wait_limit);
   return cudaGetLastError();
 }

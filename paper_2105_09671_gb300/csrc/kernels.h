@@ -115,7 +115,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 int ac_validate_desc(const ac_grid_desc *d);
-int ac_default_depth(int ndim, int dtype);  // temporal-block depth of the default schedule
+int ac_default_depth(const ac_grid_desc *d);  // temporal-block depth of the default schedule
 bool ac_plan_depths(int64_t n, int k, std::vector<int> &depths);
 EncodeTiledFn ac_encode_fn();
 CUtensorMapDataType ac_tmap_type(int dtype);

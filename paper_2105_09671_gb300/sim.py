@@ -213,6 +213,12 @@ class Batch:
     def schedule(self) -> int:
         return L.ac_batch_get_schedule(self.handle)
 
+    def set_tile(self, tile: int) -> None:
+        L.ac_batch_set_tile(self.handle, tile)
+
+    def tile(self) -> int:
+        return L.ac_batch_get_tile(self.handle)
+
     def autotune(self, steps_per_trial: int = 64) -> None:
         L.ac_batch_autotune(self.handle, steps_per_trial)
 

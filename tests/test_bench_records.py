@@ -25,7 +25,7 @@ def test_traffic_record_matches_the_kernel_source_it_names():
         assert "--clock-control none" in rec["command"]
         with open(src, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        got = bench.recorded_traffic(kernel, os.path.basename(src))
+        got = bench.recorded_traffic(kernel, os.path.basename(src), rec.get("grid"))
         # valid only while the source is the captured one
         assert (got == rec["dram_bytes_per_launch"]) == (sha == rec["source_sha256"])
 
@@ -39,9 +39,11 @@ def test_traffic_record_rejects_another_source(tmp_path, monkeypatch):
     sha = hashlib.sha256(b"kernel v1\n").hexdigest()
     (prof / "traffic.json").write_text(json.dumps(
         {"kern": {"source": "paper_2105_09671_gb300/csrc/k.cuh", "source_sha256": sha,
-                  "dram_bytes_per_launch": 1234}}))
+                  "dram_bytes_per_launch": 1234, "grid": [8, 16]}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.recorded_traffic("kern", "k.cuh") == 1234
+    assert bench.recorded_traffic("kern", "k.cuh", (8, 16)) == 1234
+    assert bench.recorded_traffic("kern", "k.cuh", (16, 16)) is None  # another grid
     assert bench.recorded_traffic("other", "k.cuh") is None
     (csrc / "k.cuh").write_text("kernel v2\n")
     assert bench.recorded_traffic("kern", "k.cuh") is None

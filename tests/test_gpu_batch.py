@@ -29,14 +29,19 @@ def _specs(shapes, seed=0):
 SHAPES = [(1, 1), (3, 130), (64, 64), (97, 33), (130, 250), (200, 121), (257, 257), (40, 300)]
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64", "f16s"])
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
-def test_batch_equals_single_grid_stepper_bitwise(dtype, k):
+BATCH_SCHEDULES = [(d, k, 0) for d in ("f32", "f64", "f16s") for k in (1, 2, 3, 4)] + \
+    [("f32", k, 1) for k in (1, 2, 3, 4, 5, 6)]
+
+
+@pytest.mark.parametrize("dtype,k,tile", BATCH_SCHEDULES)
+def test_batch_equals_single_grid_stepper_bitwise(dtype, k, tile):
     specs, inits = _specs(SHAPES, seed=k)
     n = [5, 0, 1, 2 * k + 1, 37, 64, 13, 9]
     b = ac.Batch(specs, dtype=dtype)
     try:
+        b.set_tile(tile)
         b.set_schedule(k)
+        assert b.tile() == tile
         for i, a in enumerate(inits):
             b.load(i, a)
         b.step(n)
@@ -57,6 +62,28 @@ def test_batch_equals_single_grid_stepper_bitwise(dtype, k):
         assert np.array_equal(got[i], ref), f"instance {i} {shp} n={n[i]}"
         o = oracle.step(stored(a, dtype), h, eps, dt, n[i])
         assert_parity(got[i].astype(np.float64), o, dtype, f"instance {i} vs oracle")
+
+
+def test_batch_tile_selection_api():
+    specs, _ = _specs(SHAPES[2:4], seed=1)
+    b32 = ac.Batch(specs, dtype="f32")
+    b16 = ac.Batch(specs, dtype="f16s")
+    try:
+        assert b32.tile() == 0
+        with pytest.raises(ac.AcError) as e:
+            b32.set_schedule(5)          # depth 5 needs the 8-cell strips
+        assert e.value.code == ac.AC_ERR_INVALID
+        b32.set_tile(1)
+        b32.set_schedule(6)
+        with pytest.raises(ac.AcError) as e:
+            b32.set_tile(0)              # depth 6 is not offered with tile 0
+        assert e.value.code == ac.AC_ERR_UNSUPPORTED
+        with pytest.raises(ac.AcError) as e:
+            b16.set_tile(1)
+        assert e.value.code == ac.AC_ERR_UNSUPPORTED
+    finally:
+        b16.close()
+        b32.close()
 
 
 def test_batch_uneven_workload_2000_steps_against_oracle():
@@ -100,8 +127,8 @@ def test_batched_workload_sampled_instances_against_oracle():
         for i, a in enumerate(inits):
             b.load(i, a)
         b.autotune(64)  # restores the fields it times on
-        k = b.schedule()
-        assert 1 <= k <= 4
+        k, tile = b.schedule(), b.tile()
+        assert 1 <= k <= (4 if tile == 0 else 6)
         b.set_graph(True)
         b.step(2000)
         assert b.status() == ac.AC_OK
@@ -116,7 +143,7 @@ def test_batched_workload_sampled_instances_against_oracle():
         worst = max(worst, rel)
         assert rel <= 1e-3, f"instance {i} (n = {d['n']}): rel-L2 {rel:.2e}"
         assert float(np.max(np.abs(got[int(i)] - o))) <= 1e-4
-    print(f"\nbatch512: autotuned k = {k}; 16 sampled instances, worst rel-L2 {worst:.2e}")
+    print(f"\nbatch512: autotuned k = {k}, tile {tile}; 16 sampled instances, worst rel-L2 {worst:.2e}")
 
 
 def test_batch_graph_replay_and_launch_count():

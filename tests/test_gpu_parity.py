@@ -195,8 +195,10 @@ def test_tile_selection_api():
     sim2 = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim3 = ac.Simulation((8, 16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim2h = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f16s")
+    big = ac.Simulation((1024, 1024), 1 / 1024, 4 / 1024, 0.1 / 1024 ** 2, dtype="f32")
     try:
-        assert sim2.tile() == 0
+        assert sim2.tile() == 0 and sim2.schedule() == (ac.AC_VARIANT_STREAM, 4)
+        assert big.tile() == 1 and big.schedule() == (ac.AC_VARIANT_STREAM, 6)  # 8-cell strips from 1024^2
         sim2.set_tile(0)
         sim2.set_tile(1)             # FP32 2D: strips of 8 cells per lane
         assert sim2.tile() == 1
@@ -218,6 +220,7 @@ def test_tile_selection_api():
         sim3.set_tile(ac.AC_TILE_AUTO)
         assert sim3.tile() in range(ac.AC_NUM_TILES_3D)
     finally:
+        big.close()
         sim2h.close()
         sim2.close()
         sim3.close()

@@ -33,7 +33,8 @@ int set_error(int code, const char *msg) {
   return code;
 }
 
-cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ) {
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ,
+                         int carveout) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -56,6 +57,10 @@ cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int sme
   }
   e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  if (carveout >= 0) {
+    e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+    if (e != cudaSuccess) return e;
+  }
   int n = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
   if (e != cudaSuccess) return e;

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 
+#include "kernels.h"
 #include "net.cuh"
 #include "tc.cuh"
 
@@ -503,22 +504,21 @@ static int grid_for(int64_t n, int per_block, int num_sms) {
   return (int)std::min<int64_t>((n + per_block - 1) / per_block, (int64_t)num_sms * 16);
 }
 
+// Dynamic shared-memory limits of the kernels that need more than the
+// default, once per device (thread-safe; the occupancy query is unused).
 template <int NDIM>
 static cudaError_t setup_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  static KernelSetup k_last_t, k_last_f, k_wgrad, k_dfin;
+  int occ = 0;
   cudaError_t e;
-  e = cudaFuncSetAttribute(net_last_fwd_k<NDIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, last_smem_bytes<NDIM>());
+  e = kernel_setup(k_last_t, (const void *)net_last_fwd_k<NDIM, true>, 32, last_smem_bytes<NDIM>(), &occ);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(net_last_fwd_k<NDIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, last_smem_bytes<NDIM>());
+  e = kernel_setup(k_last_f, (const void *)net_last_fwd_k<NDIM, false>, 32, last_smem_bytes<NDIM>(), &occ);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(net_wgrad_tc_k<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, WgradGeom<NDIM>::SMEM);
+  e = kernel_setup(k_wgrad, (const void *)net_wgrad_tc_k<NDIM>, 32, WgradGeom<NDIM>::SMEM, &occ);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(net_dgrad_finish_k<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           net_taps(NDIM) * kNetC * kNetC * 4);
-  if (e != cudaSuccess) return e;
-  done = true;
-  return cudaSuccess;
+  return kernel_setup(k_dfin, (const void *)net_dgrad_finish_k<NDIM>, 32,
+                      net_taps(NDIM) * kNetC * kNetC * 4, &occ);
 }
 
 template <int NDIM>

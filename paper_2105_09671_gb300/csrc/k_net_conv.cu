@@ -323,21 +323,14 @@ static cudaError_t conv_rows_t(const bf16 *in, const bf16 *Wx, const float *bias
                                const NetShape &sh, bf16 *zout, bf16 *outpad, float *outraw,
                                int *status, int num_sms, cudaStream_t s) {
   using Gm = CvGeom<NDIM>;
-  static int occ = 0;
-  if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(net_conv_rows_k<NDIM, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(net_conv_rows_k<NDIM, MODE>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_conv_rows_k<NDIM, MODE>,
-                                                      kCvThreads, Gm::SMEM);
-    if (e != cudaSuccess) return e;
-    // the register budget of __launch_bounds__ guarantees MINB CTAs per SM
-    // (the shared memory fits as well); the query may report fewer
-    occ = std::max(occ, Gm::MINB);
-  }
+  static KernelSetup ks;
+  int occ = 1;
+  cudaError_t e0 = kernel_setup(ks, (const void *)net_conv_rows_k<NDIM, MODE>, kCvThreads, Gm::SMEM,
+                                &occ, 100);
+  if (e0 != cudaSuccess) return e0;
+  // the register budget of __launch_bounds__ guarantees MINB CTAs per SM
+  // (the shared memory fits as well); the query may report fewer
+  occ = std::max(occ, Gm::MINB);
   // the padded activations as a 2D tensor {32 channels, padded pixels}
   const int64_t P = sh.padded_cells();
   if (P + 2 * kCvPix >= (int64_t)INT32_MAX) return cudaErrorInvalidValue;

@@ -2,6 +2,7 @@
 // operands and FP32 accumulation (tcgen05, one 128-row tile per CTA).  It is
 // the building block of the learned stepper's convolutions, exposed so that
 // the operand layouts and descriptors can be checked on their own.
+#include "kernels.h"
 #include "tc.cuh"
 
 namespace ac {
@@ -72,13 +73,10 @@ __global__ void __launch_bounds__(128) tc_gemm_n32_k(const __nv_bfloat16 *__rest
 cudaError_t launch_tc_gemm_n32(const void *a, const void *b, float *d, int64_t m, int k, int *status,
                                cudaStream_t s) {
   const int smem = 160 * k * 2 + 16;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_n32_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         160 * 512 * 2 + 16);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static KernelSetup ks;
+  int occ = 0;
+  cudaError_t e = kernel_setup(ks, (const void *)tc_gemm_n32_k, 128, 160 * 512 * 2 + 16, &occ);
+  if (e != cudaSuccess) return e;
   tc_gemm_n32_k<<<(unsigned)(m / 128), 128, smem, s>>>((const __nv_bfloat16 *)a,
                                                         (const __nv_bfloat16 *)b, d, k, status);
   return cudaGetLastError();

@@ -105,7 +105,9 @@ constexpr int kSetupDevices = 64;
 struct KernelSetup {
   std::atomic<int> occ[kSetupDevices];  // 0 = not set up on that device yet
 };
-cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ);
+// carveout >= 0 also sets the preferred shared-memory carveout (percent).
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int threads, int smem, int *occ,
+                         int carveout = -1);
 
 }  // namespace ac
 

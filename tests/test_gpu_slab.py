@@ -96,3 +96,42 @@ def test_sphere_512_in_two_slabs_matches_the_whole_grid():
     finally:
         slab.close()
         whole.close()
+
+
+def test_distributed_slab_on_device_single_rank():
+    # the one-rank-per-part layer on a device: with one rank there is nothing
+    # to exchange, and the part is the whole grid stepped by its Simulation
+    import os
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_2105_09671_gb300.slab import DistributedSlab
+    if dist.is_initialized():
+        pytest.skip("a process group already exists")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        shape = (24, 20, 36)
+        h = 1.0 / 36
+        eps, dt = 3.0 * h, 0.1 * h * h
+        phi0 = _field(shape, seed=4)
+        ds, sim = DistributedSlab.on_device(shape, h, eps, dt, halo=4, dtype="f32")
+        whole = ac.Simulation(shape, h, eps, dt, dtype="f32")
+        try:
+            assert (ds.own_lo, ds.own_hi, ds.ext_lo, ds.ext_hi) == (0, 24, 0, 24)
+            sim.load(phi0)
+            ds.mark_fresh()
+            ds.step(10)
+            whole.load(phi0)
+            whole.step(10)
+            assert ds.exchanges == 0
+            torch.cuda.synchronize()
+            assert np.array_equal(sim.to_numpy(), whole.to_numpy())
+            assert torch.equal(ds.owned()[:, :, :36].cpu(), torch.from_numpy(sim.to_numpy()))
+        finally:
+            whole.close()
+            sim.close()
+    finally:
+        dist.destroy_process_group()

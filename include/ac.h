@@ -205,18 +205,22 @@ int ac_set_tile(ac_ctx *ctx, int32_t tile);
 int ac_get_tile(ac_ctx *ctx, int32_t *tile);
 
 /* Time the candidate (variant, k, tile) schedules on the context's own buffers
- * with CUDA events (about steps_per_trial steps each) and keep the fastest.
+ * with CUDA events (about steps_per_trial steps each) and keep the fastest;
+ * a context with graph replay on (ac_set_graph) has each candidate timed as
+ * a replayed graph, the way its steps will run.
  * phi is saved to a temporary device buffer that this call allocates and
  * frees, and restored after every trial, so the field is unchanged.  The
- * choice is cached per (ndim, dtype, log2 of the cell count, device model)
- * for the process lifetime (and in a file, see ac_set_tune_cache); later
+ * choice is cached per (ndim, dtype, log2 of the cell count, device model,
+ * graph replay on or off) for the process lifetime (and in a file, see ac_set_tune_cache); later
  * contexts of the same class reuse it without timing.  Synchronises the
  * stream. */
 int ac_autotune(ac_ctx *ctx, int64_t steps_per_trial);
 
 /* Keep autotuning results in a text file as well (one line per choice:
- * "ac-tune-v1 ndim dtype size_class device variant k tile", device = the
- * model name and SM count), so that later processes skip the timing:
+ * "ac-tune-v2 ndim dtype size_class device graph variant k tile", device =
+ * the model name and SM count, graph = 1 for choices timed as graph
+ * replays; lines of the earlier v1 form, without the graph field, are read
+ * as graph = 0), so that later processes skip the timing:
  * ac_autotune first looks in the process cache, then in the file, and
  * appends what it measures.  NULL or "" stops using a file.  Also empties
  * the process cache.  An unreadable file is treated as empty and a failed

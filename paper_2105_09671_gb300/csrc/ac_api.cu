@@ -553,8 +553,9 @@ namespace {
 struct TuneKey {
   int ndim, dtype, cls;
   std::string device;
+  int graph;  // timed as graph replay (1) or as launches (0)
   bool operator<(const TuneKey &o) const {
-    return std::tie(ndim, dtype, cls, device) < std::tie(o.ndim, o.dtype, o.cls, o.device);
+    return std::tie(ndim, dtype, cls, device, graph) < std::tie(o.ndim, o.dtype, o.cls, o.device, o.graph);
   }
 };
 std::mutex g_tune_mu;
@@ -574,8 +575,10 @@ std::string device_key(int device) {
 }
 
 // File format, one entry per line:
-//   ac-tune-v1 <ndim> <dtype> <size class> <device> <variant> <k> <tile>
-// Unreadable lines are skipped; the last entry for a key wins.
+//   ac-tune-v2 <ndim> <dtype> <size class> <device> <graph> <variant> <k> <tile>
+// (lines of the earlier "ac-tune-v1" form, without <graph>, are choices
+// timed as launches).  Unreadable lines are skipped; the last entry for a
+// key wins.
 bool file_lookup(const TuneKey &key, TuneChoice *out) {
   if (g_tune_file.empty()) return false;
   FILE *f = fopen(g_tune_file.c_str(), "r");
@@ -583,11 +586,18 @@ bool file_lookup(const TuneKey &key, TuneChoice *out) {
   char line[512], tag[32], dev[256];
   bool found = false;
   while (fgets(line, sizeof line, f)) {
-    int nd, dt, cls, v, k, t;
-    if (sscanf(line, "%31s %d %d %d %255s %d %d %d", tag, &nd, &dt, &cls, dev, &v, &k, &t) != 8)
+    int nd, dt, cls, gr, v, k, t;
+    if (sscanf(line, "%31s", tag) != 1) continue;
+    if (strcmp(tag, "ac-tune-v2") == 0) {
+      if (sscanf(line, "%31s %d %d %d %255s %d %d %d %d", tag, &nd, &dt, &cls, dev, &gr, &v, &k, &t) != 9)
+        continue;
+    } else if (strcmp(tag, "ac-tune-v1") == 0) {
+      if (sscanf(line, "%31s %d %d %d %255s %d %d %d", tag, &nd, &dt, &cls, dev, &v, &k, &t) != 8) continue;
+      gr = 0;
+    } else {
       continue;
-    if (strcmp(tag, "ac-tune-v1") != 0) continue;
-    if (nd == key.ndim && dt == key.dtype && cls == key.cls && key.device == dev) {
+    }
+    if (nd == key.ndim && dt == key.dtype && cls == key.cls && key.device == dev && gr == key.graph) {
       *out = TuneChoice{v, k, t};
       found = true;
     }
@@ -600,8 +610,8 @@ void file_append(const TuneKey &key, const TuneChoice &c) {
   if (g_tune_file.empty()) return;
   FILE *f = fopen(g_tune_file.c_str(), "a");
   if (!f) return;
-  fprintf(f, "ac-tune-v1 %d %d %d %s %d %d %d\n", key.ndim, key.dtype, key.cls, key.device.c_str(),
-          c.variant, c.k, c.tile);
+  fprintf(f, "ac-tune-v2 %d %d %d %s %d %d %d %d\n", key.ndim, key.dtype, key.cls, key.device.c_str(),
+          key.graph, c.variant, c.k, c.tile);
   fclose(f);
 }
 }  // namespace
@@ -614,7 +624,8 @@ static int size_class(const ac_grid_desc &d) {
 extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   if (!c) return fail(AC_ERR_INVALID, "ctx is NULL");
   if (steps_per_trial < 1) return fail(AC_ERR_INVALID, "steps_per_trial must be >= 1");
-  const TuneKey key{c->d.ndim, c->d.dtype, size_class(c->d), device_key(c->device)};
+  const TuneKey key{c->d.ndim, c->d.dtype, size_class(c->d), device_key(c->device),
+                    (c->use_graph && c->stream != nullptr) ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -644,16 +655,46 @@ extern "C" int ac_autotune(ac_ctx *c, int64_t steps_per_trial) {
   float best = 1e30f;
   TuneChoice best_c = cand.front();
   cudaMemcpyAsync(backup, c->phi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  // A context that replays its steps through a CUDA graph has them timed the
+  // same way (small grids are bound by launch overhead, which graphs remove).
+  const bool graphed = c->use_graph && c->stream != nullptr;
   for (auto &cd : cand) {
     // steps rounded to a multiple of 2k so every candidate runs full passes
     const int64_t n = std::max<int64_t>(2 * cd.k, steps_per_trial / (2 * cd.k) * (2 * cd.k));
     rc = issue_steps(c, 2 * cd.k, cd.variant, cd.k, cd.tile);  // warm-up
     if (rc) break;
+    cudaGraphExec_t gx = nullptr;
+    if (graphed) {
+      cudaGraph_t gr = nullptr;
+      const int64_t before = c->launches;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        rc = fail(AC_ERR_CUDA, "stream capture failed");
+        break;
+      }
+      rc = issue_steps(c, n, cd.variant, cd.k, cd.tile);
+      const cudaError_t ec = cudaStreamEndCapture(c->stream, &gr);
+      c->launches = before;
+      if (rc == AC_OK && ec != cudaSuccess) rc = fail(AC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+      if (rc == AC_OK && cudaGraphInstantiate(&gx, gr, 0) != cudaSuccess)
+        rc = fail(AC_ERR_CUDA, "graph instantiate failed");
+      if (gr) cudaGraphDestroy(gr);
+      if (rc == AC_OK && cudaGraphLaunch(gx, c->stream) != cudaSuccess)  // warm-up replay
+        rc = fail(AC_ERR_CUDA, "graph launch failed");
+      if (rc) {
+        if (gx) cudaGraphExecDestroy(gx);
+        break;
+      }
+    }
     cudaEventRecord(e0, c->stream);
-    rc = issue_steps(c, n, cd.variant, cd.k, cd.tile);
-    if (rc) break;
+    if (graphed) {
+      if (cudaGraphLaunch(gx, c->stream) != cudaSuccess) rc = fail(AC_ERR_CUDA, "graph launch failed");
+    } else {
+      rc = issue_steps(c, n, cd.variant, cd.k, cd.tile);
+    }
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
+    if (gx) cudaGraphExecDestroy(gx);
+    if (rc) break;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     const float per_step = ms / (float)n;

@@ -93,15 +93,19 @@ def test_tune_cache_file_round_trip(tmp_path):
             sim.close()
         lines = path.read_text().splitlines()
         assert len(lines) == 1
-        tag, nd, dt_code, cls, dev, v, k, t = lines[0].split()
-        assert tag == "ac-tune-v1" and int(nd) == 3 and int(dt_code) == ac.AC_F32
+        tag, nd, dt_code, cls, dev, gr, v, k, t = lines[0].split()
+        assert tag == "ac-tune-v2" and int(nd) == 3 and int(dt_code) == ac.AC_F32 and int(gr) == 0
         assert (int(v), int(k)) == tuned[0] and int(t) == tuned[1]
         # a later entry for the same key wins: a new process (emulated by
-        # emptying the process cache) adopts it without timing
+        # emptying the process cache) adopts it without timing; an entry of
+        # the earlier v1 form (no graph field) counts as timed without graphs,
+        # and an entry for graph replay does not apply to this context
         other = (ac.AC_VARIANT_DIRECT, 1, 0) if tuned[0][0] == ac.AC_VARIANT_STREAM \
             else (ac.AC_VARIANT_STREAM, 1, 0)
+        third = (ac.AC_VARIANT_STREAM, 2, 2)
         with open(path, "a") as f:
             f.write(f"ac-tune-v1 {nd} {dt_code} {cls} {dev} {other[0]} {other[1]} {other[2]}\n")
+            f.write(f"ac-tune-v2 {nd} {dt_code} {cls} {dev} 1 {third[0]} {third[1]} {third[2]}\n")
             f.write("not a cache line\n")
         ac.ac_set_tune_cache(str(path))
         sim = ac.Simulation(shape, h, eps, dt, dtype="f32", stream=s)
@@ -112,5 +116,42 @@ def test_tune_cache_file_round_trip(tmp_path):
             assert sim.schedule() == other[:2] and sim.tile() == other[2]
         finally:
             sim.close()
+        ac.ac_set_tune_cache(str(path))
+        sim = ac.Simulation(shape, h, eps, dt, dtype="f32", stream=s)
+        try:
+            sim.set_graph(True)  # the graph-replay entry applies now
+            n0 = sim.launch_count()
+            sim.autotune(4)
+            assert sim.launch_count() == n0
+            assert sim.schedule() == third[:2] and sim.tile() == third[2]
+        finally:
+            sim.close()
     finally:
         ac.ac_set_tune_cache(None)
+
+
+def test_autotune_with_graph_replay_times_graphs():
+    # a small grid is bound by launch overhead; with graph replay on, the
+    # candidates are timed as replayed graphs (the field is kept) and the
+    # choice is cached apart from the one timed as launches
+    import torch
+    shape = (64, 64)
+    h = 1.0 / 64
+    eps, dt = 0.015, 0.1 * h * h
+    phi0 = wl.smooth_field(shape, seed=3)
+    s = torch.cuda.Stream()
+    ac.ac_set_tune_cache(None)
+    sim = ac.Simulation(shape, h, eps, dt, dtype="f64", stream=s)
+    try:
+        sim.load(phi0)
+        before = sim.to_numpy().copy()
+        sim.set_graph(True)
+        sim.autotune(32)
+        assert np.array_equal(sim.to_numpy(), before)
+        v, k = sim.schedule()
+        sim.step(40)
+        assert sim.status() == ac.AC_OK
+        out = sim.to_numpy().astype(np.float64)
+    finally:
+        sim.close()
+    assert_parity(out, oracle_run(phi0, h, eps, dt, 40, "f64"), "f64", f"graph-tuned v{v} k{k}")

@@ -648,16 +648,20 @@ def run_ours(args, ws, rank, local):
     dist_barrier(ws, device)
     torch.cuda.synchronize(device)
     s_s, s_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ph = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(e2e_steps)]
     s_s.record(stream)
     for i in range(e2e_steps):
         with torch.cuda.stream(stream):
             sim.phi.copy_(host_in, non_blocking=True)
+        ph[i][0].record(stream)
         sim.step(w.steps)
+        ph[i][1].record(stream)
         with torch.cuda.stream(stream):
             host_out[0].copy_(sim.phi, non_blocking=True)
     s_e.record(stream)
     torch.cuda.synchronize(device)
     single_ms = dist_max(ws, s_s.elapsed_time(s_e), device)
+    steps_ms = sum(ph[i][0].elapsed_time(ph[i][1]) for i in range(e2e_steps))
     single_value = w.cells * w.steps * e2e_steps * ws / (single_ms / 1e3) / 1e9
     if not torch.isfinite(host_out[0]).all():
         raise RuntimeError("end-to-end job produced a non-finite field")
@@ -722,6 +726,7 @@ def run_ours(args, ws, rank, local):
                      "effective_frac_k1": value / ws * 2 * es / peak},
         "e2e": {"value": single_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes, "jobs": e2e_steps,
+                "ms_per_job": single_ms / e2e_steps, "steps_ms_per_job": steps_ms / e2e_steps,
                 "how": "one job at a time on one stream: H2D of the initial field from pinned "
                        "memory, the Euler steps, D2H of the final field"},
         "e2e_pipelined": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes,

@@ -519,6 +519,77 @@ def run_learned(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_slab(args, ws, rank, local):
+    """The 512^3 sphere job through the slab decomposition on one GPU: the
+    grid split along z into --parts parts with halo planes, each part
+    stepped by its own context, halos refreshed by device copies between
+    blocks, the whole sequence replayed as one CUDA graph (and, beside it,
+    launched one by one); the same job undivided (graph replay) beside it."""
+    import torch
+    import paper_2105_09671_gb300 as ac
+    from paper_2105_09671_gb300.slab import Slab
+
+    w, dtype, _, _ = workload("sphere512")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device)
+    slab = Slab(w.shape, w.h, w.eps, w.dt, parts=args.parts, dtype=dtype, device=device, stream=stream)
+    whole = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype=dtype, device=device, stream=stream)
+    whole.set_graph(True)
+
+    def job_slab():
+        slab.full.init_sphere(r0=w.r0)
+        slab.scatter()
+        slab.step(w.steps)
+        slab.gather()
+
+    def job_slab_direct():
+        slab.set_graph(False)
+        job_slab()
+        slab.set_graph(True)
+
+    def job_whole():
+        whole.init_sphere(r0=w.r0)
+        whole.step(w.steps)
+
+    res = {}
+    slab.set_graph(True)
+    for name, job in (("slab_direct", job_slab_direct), ("slab", job_slab), ("whole", job_whole)):
+        for _ in range(args.warmup):
+            job()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            job()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        res[name] = e0.elapsed_time(e1) / args.steps
+    k0, c0 = slab.launch_count()
+    job_slab()
+    kernels, copies = slab.launch_count()
+    kernels, copies = kernels - k0, copies - c0
+    with torch.cuda.stream(stream):
+        equal = bool(torch.equal(slab.full.phi, whole.phi))
+    torch.cuda.synchronize(device)
+    halo = slab.halo
+    slab.close()
+    whole.close()
+    value = w.cells * w.steps / (res["slab"] / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["slab"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": "sphere3d_512_slabs", "parts": args.parts, "halo": halo,
+                       "split": "z", "exchange": "device-to-device plane copies on the stream",
+                       "graph": True},
+            "undivided_ms": res["whole"], "overhead": res["slab"] / res["whole"] - 1.0,
+            "slab_launched_one_by_one_ms": res["slab_direct"],
+            "bitwise_equal_to_undivided": equal, "kernels_and_copies_per_job": [kernels, copies],
+        }), flush=True)
+
+
 def run_reference(args, ws, rank):
     """The oracle arm: the FP64 C oracle on the host cores, same workload."""
     if rank != 0:
@@ -782,7 +853,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sphere512",
-                    choices=["sphere512", "separation4096", "batch512", "learned1024"])
+                    choices=["sphere512", "separation4096", "batch512", "learned1024", "slab512"])
+    ap.add_argument("--parts", type=int, default=2, help="slab512: parts along z")
     ap.add_argument("--train-iters", type=int, default=0,
                     help="learned workload: Adam steps of the 2D network (0: from --train-trajectories)")
     ap.add_argument("--train-trajectories", type=int, default=2000)
@@ -809,6 +881,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "learned1024":
         run_learned(args, ws, rank, local)
+    elif args.workload == "slab512":
+        run_slab(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -538,6 +538,11 @@ int ac_slab_gather(ac_slab *slab, void *phi_dev);
 int ac_slab_step(ac_slab *slab, int64_t n);
 /* Schedule of every part (as ac_set_schedule). */
 int ac_slab_set_schedule(ac_slab *slab, int32_t variant, int32_t k);
+/* Replay ac_slab_step through a CUDA graph: the whole sequence for n steps
+ * (every part's launches and the halo copies) is captured on the first call
+ * with that n (and halo state) and replayed afterwards.  Needs a
+ * non-default stream (AC_ERR_UNSUPPORTED otherwise); enable = 0 drops it. */
+int ac_slab_set_graph(ac_slab *slab, int32_t enable);
 /* Plan entry, halo depth and field of one part (its layout: desc with the
  * slow axis extent ext_hi - ext_lo). */
 int ac_slab_get_part(ac_slab *slab, int32_t part, ac_slab_part *plan, int32_t *halo, void **phi_dev);

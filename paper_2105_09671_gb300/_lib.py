@@ -41,7 +41,8 @@ EXPORTED = (
     "ac_net_launch_count", "ac_net_destroy", "ac_learned_advance", "ac_net_train",
     "ac_net_init_params", "ac_jump_residual", "ac_jump_spot_check", "ac_net_calibrate_guard",
     "ac_slab_plan", "ac_slab_create", "ac_slab_scatter", "ac_slab_gather", "ac_slab_step",
-    "ac_slab_set_schedule", "ac_slab_get_part", "ac_slab_launch_count", "ac_slab_destroy",
+    "ac_slab_set_schedule", "ac_slab_set_graph", "ac_slab_get_part", "ac_slab_launch_count",
+    "ac_slab_destroy",
 )
 
 
@@ -211,6 +212,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "ac_slab_gather": [vp, vp],
         "ac_slab_step": [vp, i64],
         "ac_slab_set_schedule": [vp, i32, i32],
+        "ac_slab_set_graph": [vp, i32],
         "ac_slab_get_part": [vp, i32, ctypes.POINTER(AcSlabPart), ctypes.POINTER(i32), ctypes.POINTER(vp)],
         "ac_slab_launch_count": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "ac_slab_destroy": [vp],
@@ -594,6 +596,10 @@ def ac_slab_step(slab: int, n: int) -> None:
 
 def ac_slab_set_schedule(slab: int, variant: int, k: int) -> None:
     check(lib().ac_slab_set_schedule(ctypes.c_void_p(slab), int(variant), int(k)))
+
+
+def ac_slab_set_graph(slab: int, enable: bool) -> None:
+    check(lib().ac_slab_set_graph(ctypes.c_void_p(slab), int(bool(enable))))
 
 
 def ac_slab_get_part(slab: int, part: int) -> tuple:

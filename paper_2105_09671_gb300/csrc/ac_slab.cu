@@ -44,6 +44,8 @@ struct SlabPart {
   ac_slab_part plan{};
   void *phi = nullptr, *ws = nullptr;
   ac_ctx *ctx = nullptr;
+  int64_t graph_kernels = 0;  // kernels of this part in the captured graph
+  int64_t extra = 0;          // correction of the context's own launch count
 };
 
 struct ac_slab {
@@ -54,13 +56,26 @@ struct ac_slab {
   std::vector<SlabPart> part;
   bool fresh = false;      // halos hold their neighbours' current owned planes
   int64_t copies = 0;
+  // graph replay of ac_slab_step: the sequence for (n, fresh at the start)
+  bool use_graph = false;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_n = -1;
+  bool graph_fresh = false;
+  int64_t graph_copies = 0;
 };
+
+static void slab_release_graph(ac_slab *s) {
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
+  s->graph_n = -1;
+}
 
 static char *at(void *base, int64_t planes, size_t plane_bytes) {
   return static_cast<char *>(base) + (size_t)planes * plane_bytes;
 }
 
 static void slab_free(ac_slab *s) {
+  slab_release_graph(s);
   for (SlabPart &p : s->part) {
     if (p.ctx) ac_destroy(p.ctx);
     cudaFree(p.phi);
@@ -161,9 +176,7 @@ static int exchange(ac_slab *s) {
   return AC_OK;
 }
 
-extern "C" int ac_slab_step(ac_slab *s, int64_t n) {
-  if (!s) return sfail(AC_ERR_INVALID, "slab is NULL");
-  if (n < 0) return sfail(AC_ERR_INVALID, "n must be >= 0");
+static int slab_issue(ac_slab *s, int64_t n) {
   while (n > 0) {
     const int64_t b = n < s->halo ? n : s->halo;
     if (!s->fresh) {
@@ -180,8 +193,69 @@ extern "C" int ac_slab_step(ac_slab *s, int64_t n) {
   return AC_OK;
 }
 
+extern "C" int ac_slab_step(ac_slab *s, int64_t n) {
+  if (!s) return sfail(AC_ERR_INVALID, "slab is NULL");
+  if (n < 0) return sfail(AC_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return AC_OK;
+  if (!s->use_graph || s->stream == nullptr) return slab_issue(s, n);
+  // the whole sequence (blocks, halo copies) as one graph, captured once per
+  // (n, whether the halos are fresh at the start)
+  if (!s->graph || s->graph_n != n || s->graph_fresh != s->fresh) {
+    slab_release_graph(s);
+    const bool fresh0 = s->fresh;
+    const int64_t copies0 = s->copies;
+    std::vector<int64_t> launches0;
+    for (SlabPart &p : s->part) {
+      int64_t c = 0;
+      ac_launch_count(p.ctx, &c);
+      launches0.push_back(c);
+    }
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return sfail(AC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    int rc = slab_issue(s, n);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->stream, &g);
+    s->graph_copies = s->copies - copies0;
+    s->copies = copies0;
+    s->fresh = fresh0;  // the capture only recorded the sequence
+    if (rc == AC_OK && e != cudaSuccess) rc = sfail(AC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    if (rc == AC_OK && cudaGraphInstantiate(&s->graph, g, 0) != cudaSuccess) {
+      s->graph = nullptr;
+      rc = sfail(AC_ERR_CUDA, "graph instantiate failed");
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    s->graph_n = n;
+    s->graph_fresh = fresh0;
+    // the part contexts counted their captured kernels as launched: the
+    // replays below count them instead
+    for (size_t i = 0; i < s->part.size(); ++i) {
+      int64_t c = 0;
+      ac_launch_count(s->part[i].ctx, &c);
+      s->part[i].graph_kernels = c - launches0[i];
+      s->part[i].extra -= s->part[i].graph_kernels;
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(s->graph, s->stream);
+  if (e != cudaSuccess) return sfail(AC_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(e));
+  for (SlabPart &p : s->part) p.extra += p.graph_kernels;
+  s->copies += s->graph_copies;
+  if (s->parts > 1) s->fresh = false;
+  return AC_OK;
+}
+
+extern "C" int ac_slab_set_graph(ac_slab *s, int32_t enable) {
+  if (!s) return sfail(AC_ERR_INVALID, "slab is NULL");
+  if (enable && s->stream == nullptr)
+    return sfail(AC_ERR_UNSUPPORTED, "graph replay needs a non-default stream");
+  s->use_graph = enable != 0;
+  if (!s->use_graph) slab_release_graph(s);
+  return AC_OK;
+}
+
 extern "C" int ac_slab_set_schedule(ac_slab *s, int32_t variant, int32_t k) {
   if (!s) return sfail(AC_ERR_INVALID, "slab is NULL");
+  slab_release_graph(s);
   for (SlabPart &p : s->part) {
     int rc = ac_set_schedule(p.ctx, variant, k);
     if (rc) return rc;
@@ -204,7 +278,7 @@ extern "C" int ac_slab_launch_count(ac_slab *s, int64_t *kernels, int64_t *copie
   for (SlabPart &p : s->part) {
     int64_t c = 0;
     ac_launch_count(p.ctx, &c);
-    k += c;
+    k += c + p.extra;
   }
   if (kernels) *kernels = k;
   if (copies) *copies = s->copies;

@@ -65,6 +65,9 @@ class Slab:
     def set_schedule(self, variant: int, k: int) -> None:
         L.ac_slab_set_schedule(self.handle, variant, k)
 
+    def set_graph(self, enable: bool) -> None:
+        L.ac_slab_set_graph(self.handle, enable)
+
     def part(self, i: int) -> tuple:
         return L.ac_slab_get_part(self.handle, i)
 

@@ -135,3 +135,40 @@ def test_distributed_slab_on_device_single_rank():
             sim.close()
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("shape,parts,n", [((40, 24, 36), 3, 13), ((96, 70), 2, 37)])
+def test_slab_graph_replay_equals_direct_launches(shape, parts, n):
+    # the captured sequence (every part's launches and the halo copies) is
+    # replayed for repeated step counts and re-captured when the count or
+    # the halo state at the start changes
+    import torch
+    h = 1.0 / max(shape)
+    eps, dt = 3.0 * h, 0.1 * h * h
+    phi0 = _field(shape, seed=7)
+    stream = torch.cuda.Stream()
+    direct = Slab(shape, h, eps, dt, parts=parts, halo=4, dtype="f32", stream=stream)
+    graph = Slab(shape, h, eps, dt, parts=parts, halo=4, dtype="f32", stream=stream)
+    try:
+        graph.set_graph(True)
+        for sl in (direct, graph):
+            sl.load(phi0)
+            sl.step(n)       # halos fresh after the load
+            sl.step(n)       # stale halos: a second capture
+            sl.step(n)       # replay of the second
+            sl.step(n + 2)   # another count
+        assert np.array_equal(graph.to_numpy(), direct.to_numpy())
+        assert graph.launch_count() == direct.launch_count()
+    finally:
+        direct.close()
+        graph.close()
+
+
+def test_slab_graph_needs_a_stream():
+    shape = (32, 32)
+    slab = Slab(shape, 1 / 32, 3 / 32, 0.1 / 32 ** 2, parts=2, dtype="f32")
+    try:
+        with pytest.raises(RuntimeError):
+            slab.set_graph(True)
+    finally:
+        slab.close()

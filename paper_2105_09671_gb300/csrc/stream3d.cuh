@@ -16,7 +16,9 @@
 //     neighbours of others;
 //   - x neighbours come from the adjacent lane by warp shuffle (lanes own
 //     consecutive columns of a row group), the two warp-edge lanes read
-//     theirs from shared memory; y neighbours inside the thread's own rows
+//     theirs from shared memory; at k = 2 the output columns of each row
+//     group fill one warp's lanes and the halo slots whole warps after
+//     them, which form levels 1..k-1 only; y neighbours inside the thread's own rows
 //     are registers, the rows above and below its group are shared-memory
 //     reads.  The reads of level 0 (the previous input plane's stage) are
 //     issued at the start of an iteration, ahead of the wait for the new
@@ -90,6 +92,18 @@ struct S3Geom {
   static constexpr int TX = OX + 2 * HX, TXV = TX / V;
   static constexpr int TY = (OY + 2 * K + R - 1) / R * R;  // rows, whole groups of R
   static constexpr int NSLOT = TXV * (TY / R);             // (column, row group) slots
+  // Output slots: the columns of the out_x cells in the row groups that hold
+  // an output row.  When they fill whole warps (SPLIT) they take the first
+  // NA threads, row group by row group, and the halo slots the warps after
+  // them, which skip the last level (a warp-uniform branch in the same
+  // code).  Measured on GB300 at 512^3 (FP32, 256^3 FP64): +2.7 % FP32,
+  // +5.5 % FP16 storage, +4.4 % FP64 at k = 2; at k = 3 (more registers,
+  // spills) and at k = 1 (no halo warp work to save; 17 warps instead of
+  // 19) it was slower, so only k = 2 takes it.
+  static constexpr int OXV = OX / V, HXV = HX / V;
+  static constexpr int GA0 = K / R, GA1 = (K + OY + R - 1) / R;  // row groups with output rows
+  static constexpr int NA = (GA1 - GA0) * OXV;
+  static constexpr bool SPLIT = K == 2 && NA % 32 == 0 && NA < NSLOT && HXV == 1;
   static constexpr int NT = (NSLOT + 31) / 32 * 32;        // one slot per thread
   static constexpr int STAGE_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
@@ -194,15 +208,52 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
   // past the last slot duplicate it and store nothing)
   const bool qv = tid < NSLOT;
   const int qq = qv ? tid : NSLOT - 1;
-  const int qg = qq / TXV, qc = qq - qg * TXV;
+  // x neighbours come from the adjacent lane (shuffles) where it holds the
+  // adjacent column of the same rows; lsm / rsm: the left / right one is
+  // read from shared memory instead (never both)
+  int qg, qc;
+  bool lsm, rsm;
+  if constexpr (Gm::SPLIT) {
+    constexpr int OXV = Gm::OXV, HXV = Gm::HXV, GA0 = Gm::GA0, GA1 = Gm::GA1;
+    const int top = GA0 * TXV, bot = (Gm::TY / R - GA1) * TXV;
+    if (qq < Gm::NA) {
+      // output slots, OXV consecutive lanes per row group; the first and
+      // last column's outer neighbours are halo slots
+      qg = GA0 + qq / OXV;
+      const int ic = qq % OXV;
+      qc = HXV + ic;
+      lsm = ic == 0;
+      rsm = ic == OXV - 1;
+    } else if (const int h = qq - Gm::NA; h < top + bot) {
+      // whole halo rows (above, then below the output row groups), columns
+      // in consecutive lanes: the warp-edge lanes read across the warp edge
+      qg = h < top ? h / TXV : GA1 + (h - top) / TXV;
+      qc = h < top ? h % TXV : (h - top) % TXV;
+      lsm = lane == 0 && qc > 0;
+      rsm = lane == 31 && qc < TXV - 1;
+    } else {
+      // the HXV halo columns each side of the output row groups: the one
+      // neighbour that matters (towards the output columns) is read
+      const int j = (h - top - bot) % (2 * HXV);
+      qg = GA0 + (h - top - bot) / (2 * HXV);
+      qc = j < HXV ? j : OXV + j;
+      lsm = qc >= HXV + OXV;
+      rsm = qc < HXV;
+    }
+  } else {
+    qg = qq / TXV;
+    qc = qq - qg * TXV;
+    // the two warp-edge lanes read across the warp edge unless the
+    // neighbour lies outside the tile
+    lsm = lane == 0 && qc > 0;
+    rsm = lane == 31 && qc < TXV - 1;
+  }
+  // a halo warp (warp-uniform: the output slots fill whole warps)
+  const bool hw = Gm::SPLIT && tid >= Gm::NA;
   const int r0 = R * qg;
   const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
   const int64_t plane_stride = g.pitch * g.ny;
   const C alpha = (C)g.alpha, beta = (C)g.beta;
-  // the two warp-edge lanes take one x neighbour from shared memory (lane 0
-  // the left one, lane 31 the right one) unless it lies outside the tile
-  const bool lsm = lane == 0 && qc > 0;
-  const bool rsm = lane == 31 && qc < TXV - 1;
   const bool esm = lsm || rsm;
 
   // Level l keeps its last three planes in a ring of register slots: at
@@ -252,7 +303,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
     const int own = r0 * TX + qc * V;                 // row i at own + i * TX
     const int ysn = max(r0 - 1, rlo) * TX + qc * V;   // row below the group
     const int ynn = min(r0 + R, rhi) * TX + qc * V;   // row above the group
-    const int eoff = esm ? own + (lane == 0 ? -1 : V) : own;  // the edge lane's x neighbour
+    const int eoff = esm ? own + (lsm ? -1 : V) : own;  // the x neighbour read from shared memory
     const int gx0 = bx + qc * V;
     const bool lfix = gx0 == 0;               // element 0 is the x = 0 face
     const bool rfix = gx0 + V - 1 == nx - 1;  // element V-1 is the x = nx-1 face
@@ -297,6 +348,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
       }
 #pragma unroll
       for (int l = 0; l < K; ++l) {
+        if (l == K - 1 && hw) break;  // halo warps: no last level
         if (l > 0) {
           const C *cb = lvl + ((l - 1) * 3 + LR) * PLANE;
           ld_vec_c<V>(cb, ysn, ys[l]);

@@ -296,14 +296,15 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
 
 // Default 3D tile per storage type and depth, measured on GB300 (512^3
 // FP32 / FP16, 256^3 FP64): two rows per thread at 128 x 32 (tile 0) for
-// k <= 2 (FP16 storage at k = 1: several CTAs per SM, tile 1); k = 3 needs
-// the register room of four rows per thread with half the threads (tile 2).
+// k <= 2 (FP16 storage at k <= 2: two CTAs per SM, tile 1, 1150 against
+// 1114 Gcell-updates/s at k = 2); k = 3 needs the register room of four rows
+// per thread with half the threads (tile 2).
 static int default_tile(const ac_ctx *c, int k) {
   // 2D FP32 grids from 1024^2 cells on: strips of 8 cells per lane wherever
   // they are offered (k <= 6; see kWideStripCells)
   if (c->d.ndim == 2) return wide_default(&c->d) && k <= 6 ? 1 : 0;
   if (c->d.dtype == AC_F64) return k == 1 ? 0 : 2;
-  if (c->d.dtype == AC_F16S) return k == 1 ? 1 : 0;
+  if (c->d.dtype == AC_F16S) return k <= 2 ? 1 : 0;
   return k == 3 ? 2 : 0;
 }
 

@@ -191,6 +191,24 @@ def test_mirror_symmetry_3d_every_tile():
             assert np.array_equal(inv(b), a), f"v{variant} k{k} t{tile}"
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16s"])
+def test_axis_invariance_every_schedule(dtype):
+    # a field constant along one axis stays constant along it bit for bit:
+    # tile, strip, chunk and halo seams along that axis, and the faces across
+    # it, must not leak into the result
+    for shape in ((70, 530), (10, 70, 260)):
+        nd = len(shape)
+        h, eps, dt = _params(shape)
+        for axis in range(nd):
+            base = tuple(1 if a == axis else shape[a] for a in range(nd))
+            phi0 = np.repeat(wl.random_field(base, seed=axis), shape[axis], axis=axis)
+            for variant, k, tile in schedules(nd, dtype):
+                a = gpu_run(phi0, h, eps, dt, 2 * k + 1, dtype, variant, k, tile)
+                ref = np.take(a, [0], axis=axis)
+                assert np.array_equal(a, np.broadcast_to(ref, a.shape)), \
+                    f"{shape} axis {axis} v{variant} k{k} t{tile}"
+
+
 def test_tile_selection_api():
     sim2 = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim3 = ac.Simulation((8, 16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")

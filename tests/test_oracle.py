@@ -2,7 +2,7 @@
 
 None of these compares the oracle with a retyped copy of itself: hand-worked
 values, closed-form eigenmodes of the Neumann Laplacian, exact fixed points,
-bitwise grid symmetries, the 3D->2D reduction, conservation of the Laplacian,
+bitwise grid symmetries, the 3D->2D and 2D->1D reductions, conservation of the Laplacian,
 the energy gradient identity, the mean-curvature radius law and a published
 SplitMix64 known-answer sequence.
 """
@@ -129,6 +129,26 @@ def test_z_invariant_3d_equals_2d():
     o3 = oracle.step(f3, *args)
     for k in range(5):
         np.testing.assert_allclose(o3[k], o2, rtol=0, atol=1e-14)
+
+
+def test_x_only_2d_equals_the_1d_scheme():
+    # a field constant in y stays constant in y, and each row follows the 1D
+    # scheme (same Euler step, second difference with replicated ends); the
+    # 2D sum adds the y pair (S + N = 2 phi exactly) before subtracting 4 phi,
+    # so the two agree to rounding, not bitwise
+    nx, ny, n = 23, 7, 40
+    h = 1.0 / nx
+    eps, dt = 0.05, 0.1 * h * h
+    f1 = wl.random_field((1, nx), seed=12)[0]
+    got = oracle.step(np.repeat(f1[None], ny, axis=0), h, eps, dt, n)
+    ref = f1.copy()
+    for _ in range(n):
+        w = np.concatenate(([ref[0]], ref[:-1]))
+        e = np.concatenate((ref[1:], [ref[-1]]))
+        ref = ref + dt * ((ref - ref ** 3) / eps ** 2 + (w - 2.0 * ref + e) / h ** 2)
+    for j in range(ny):
+        assert np.array_equal(got[j], got[0])
+    np.testing.assert_allclose(got[0], ref, rtol=0, atol=1e-13)
 
 
 # --------------------------------------------------------------- conservation

@@ -8,12 +8,9 @@
 namespace ac {
 
 template <typename T>
-__global__ void __launch_bounds__(256) step2d_direct(const T *__restrict__ src,
-                                                     T *__restrict__ dst, GridParams g) {
+__device__ __forceinline__ void step2d_cell(const T *__restrict__ src, T *__restrict__ dst,
+                                            const GridParams &g, int64_t i, int64_t j) {
   using C = typename Traits<T>::C;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
   const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < g.nx ? i + 1 : i;
   const int64_t jm = j > 0 ? j - 1 : 0, jp = j + 1 < g.ny ? j + 1 : j;
   const T *row = src + j * g.pitch;
@@ -25,13 +22,9 @@ __global__ void __launch_bounds__(256) step2d_direct(const T *__restrict__ src,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) step3d_direct(const T *__restrict__ src,
-                                                     T *__restrict__ dst, GridParams g) {
+__device__ __forceinline__ void step3d_cell(const T *__restrict__ src, T *__restrict__ dst,
+                                            const GridParams &g, int64_t i, int64_t j, int64_t k) {
   using C = typename Traits<T>::C;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  const int64_t k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny || k >= g.nz) return;
   const int64_t im = i > 0 ? i - 1 : 0, ip = i + 1 < g.nx ? i + 1 : i;
   const int64_t jm = j > 0 ? j - 1 : 0, jp = j + 1 < g.ny ? j + 1 : j;
   const int64_t km = k > 0 ? k - 1 : 0, kp = k + 1 < g.nz ? k + 1 : k;
@@ -45,15 +38,35 @@ __global__ void __launch_bounds__(256) step3d_direct(const T *__restrict__ src,
   dst[k * plane + j * g.pitch + i] = from_c<T>(ac_update<C>(p, nsum, C(-6), C(g.alpha), C(g.beta)));
 }
 
+// one thread per x, grid-stride loops over y and z (see cell_grid)
+template <typename T>
+__global__ void __launch_bounds__(256) step2d_direct(const T *__restrict__ src,
+                                                     T *__restrict__ dst, GridParams g) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.nx) return;
+  for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
+       j += (int64_t)gridDim.y * blockDim.y)
+    step2d_cell(src, dst, g, i, j);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) step3d_direct(const T *__restrict__ src,
+                                                     T *__restrict__ dst, GridParams g) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.nx) return;
+  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
+    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
+         j += (int64_t)gridDim.y * blockDim.y)
+      step3d_cell(src, dst, g, i, j, k);
+}
+
 template <typename T>
 static cudaError_t direct_t(int ndim, const GridParams &g, const void *src, void *dst,
                             cudaStream_t s) {
-  dim3 block(64, 4);
-  dim3 grid((unsigned)((g.nx + 63) / 64), (unsigned)((g.ny + 3) / 4), 1);
+  const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
   if (ndim == 2) {
     step2d_direct<T><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
   } else {
-    grid.z = (unsigned)g.nz;
     step3d_direct<T><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
   }
   return cudaGetLastError();

@@ -38,13 +38,10 @@ template <> struct SatArg<float> { static constexpr double value = 9.5; };
 template <> struct SatArg<__half> { static constexpr double value = 6.0; };
 
 template <typename T>
-__global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, double lx, double ly,
-                              double lz, double cx, double cy, double cz, double r0,
-                              double width) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  const int64_t k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void sphere_cell(T *__restrict__ phi, const GridParams &g, int64_t i,
+                                            int64_t j, int64_t k, double h, double lx, double ly,
+                                            double lz, double cx, double cy, double cz, double r0,
+                                            double width) {
   constexpr double kSat = SatArg<T>::value;
   // Far from the interface the stored profile is exactly +-1 (|arg| >= kSat,
   // see SatArg).  An FP32 estimate of the distance decides that for most
@@ -82,18 +79,33 @@ __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, doubl
   phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
 }
 
+// one thread per x, grid-stride loops over y and z (see cell_grid)
+template <typename T>
+__global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, double lx, double ly,
+                              double lz, double cx, double cy, double cz, double r0,
+                              double width) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.nx) return;
+  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
+    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
+         j += (int64_t)gridDim.y * blockDim.y)
+      sphere_cell(phi, g, i, j, k, h, lx, ly, lz, cx, cy, cz, r0, width);
+}
+
 template <typename T>
 __global__ void init_random_k(T *__restrict__ phi, GridParams g, uint64_t seed, double amp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  const int64_t k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
-  const uint64_t c = (uint64_t)((k * g.ny + j) * g.nx + i);
-  const uint64_t z = splitmix64_at(seed, c);
-  const double u = (double)(z >> 11) * 0x1.0p-53;
-  const double r = __dsub_rn(__dmul_rn(2.0, u), 1.0);
-  const double v = __dmul_rn(amp, r);
-  phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
+  if (i >= g.nx) return;
+  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
+    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
+         j += (int64_t)gridDim.y * blockDim.y) {
+      const uint64_t c = (uint64_t)((k * g.ny + j) * g.nx + i);
+      const uint64_t z = splitmix64_at(seed, c);
+      const double u = (double)(z >> 11) * 0x1.0p-53;
+      const double r = __dsub_rn(__dmul_rn(2.0, u), 1.0);
+      const double v = __dmul_rn(amp, r);
+      phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
+    }
 }
 
 // Polar angle of the star (Section 3.1): atan(v/u) for u > 0, pi + atan(v/u)
@@ -159,20 +171,22 @@ template <typename T>
 __global__ void init_shape_k(T *__restrict__ phi, GridParams g, int kind, int ndim, double h,
                              double lx, double ly, double lz, double p0, double p1, double width) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  const int64_t k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
+  if (i >= g.nx) return;
   const double x = __dadd_rn(lx, __dmul_rn(__dadd_rn((double)i, 0.5), h));
-  const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));
-  const double z = __dadd_rn(lz, __dmul_rn(__dadd_rn((double)k, 0.5), h));
-  phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(shape_value(kind, ndim, x, y, z, p0, p1, width));
+  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
+    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
+         j += (int64_t)gridDim.y * blockDim.y) {
+      const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));
+      const double z = __dadd_rn(lz, __dmul_rn(__dadd_rn((double)k, 0.5), h));
+      phi[(k * g.ny + j) * g.pitch + i] =
+          from_f64<T>(shape_value(kind, ndim, x, y, z, p0, p1, width));
+    }
 }
 
 template <typename T>
 static cudaError_t shape_t(const GridParams &g, void *phi, int kind, int ndim, double h,
                            const double *lo, double p0, double p1, double eps, cudaStream_t s) {
-  dim3 block(64, 4);
-  dim3 grid((unsigned)((g.nx + 63) / 64), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz);
+  const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
   init_shape_k<T><<<grid, block, 0, s>>>((T *)phi, g, kind, ndim, h, lo[0], lo[1], lo[2], p0, p1,
                                          sqrt(2.0) * eps);
   return cudaGetLastError();
@@ -192,8 +206,7 @@ cudaError_t launch_init_shape(int dtype, const GridParams &g, void *phi, int kin
 template <typename T>
 static cudaError_t sphere_t(const GridParams &g, void *phi, double h, const double *lo,
                             const double *c, double r0, double eps, cudaStream_t s) {
-  dim3 block(64, 4);
-  dim3 grid((unsigned)((g.nx + 63) / 64), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz);
+  const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
   const double width = sqrt(2.0) * eps;
   init_sphere_k<T><<<grid, block, 0, s>>>((T *)phi, g, h, lo[0], lo[1], lo[2], c[0], c[1], c[2],
                                           r0, width);
@@ -203,8 +216,7 @@ static cudaError_t sphere_t(const GridParams &g, void *phi, double h, const doub
 template <typename T>
 static cudaError_t random_t(const GridParams &g, void *phi, uint64_t seed, double amp,
                             cudaStream_t s) {
-  dim3 block(64, 4);
-  dim3 grid((unsigned)((g.nx + 63) / 64), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz);
+  const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
   init_random_k<T><<<grid, block, 0, s>>>((T *)phi, g, seed, amp);
   return cudaGetLastError();
 }

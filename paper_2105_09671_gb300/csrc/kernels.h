@@ -31,6 +31,17 @@ bool stream3d_supported(int dtype, int k, int tile);
 Stream3DGeom stream3d_geom(int dtype, int k, int tile);
 
 // One step per launch, clamped global-memory neighbours (2D and 3D).
+// Launch shape of the cell-wise kernels (direct stencil, initial
+// conditions): 64 x 4 threads per block over (x, y) and one block layer per
+// z, with y and z capped at CUDA's 65535 blocks per grid dimension; the
+// kernels cover the rest of y and z by grid-stride loops.
+constexpr unsigned kCellBlockX = 64, kCellBlockY = 4;
+inline dim3 cell_grid(const GridParams &g) {
+  return dim3((unsigned)((g.nx + kCellBlockX - 1) / kCellBlockX),
+              (unsigned)std::min<int64_t>((g.ny + kCellBlockY - 1) / kCellBlockY, 65535),
+              (unsigned)std::min<int64_t>(g.nz, 65535));
+}
+
 cudaError_t launch_direct(int ndim, int dtype, const GridParams &g, const void *src, void *dst,
                           cudaStream_t s);
 // k steps per launch.  src_map describes the source field with the box of

@@ -44,6 +44,8 @@ struct SlabPart {
   ac_slab_part plan{};
   void *phi = nullptr, *ws = nullptr;
   ac_ctx *ctx = nullptr;
+  cudaStream_t stream = nullptr;  // the part's own stream (several parts)
+  cudaEvent_t done = nullptr;     // end of the part's block of steps
   int64_t graph_kernels = 0;  // kernels of this part in the captured graph
   int64_t extra = 0;          // correction of the context's own launch count
 };
@@ -53,6 +55,7 @@ struct ac_slab {
   int parts = 0, halo = 0;
   size_t plane_bytes = 0;  // bytes per plane of the slow axis (3D: pitch * ny, 2D: pitch)
   cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;  // start of a block of steps on the slab's stream
   std::vector<SlabPart> part;
   bool fresh = false;      // halos hold their neighbours' current owned planes
   int64_t copies = 0;
@@ -80,7 +83,10 @@ static void slab_free(ac_slab *s) {
     if (p.ctx) ac_destroy(p.ctx);
     cudaFree(p.phi);
     cudaFree(p.ws);
+    if (p.done) cudaEventDestroy(p.done);
+    if (p.stream) cudaStreamDestroy(p.stream);
   }
+  if (s->fork) cudaEventDestroy(s->fork);
   delete s;
 }
 
@@ -105,9 +111,23 @@ extern "C" int ac_slab_create(const ac_grid_desc *desc, int32_t parts, int32_t h
   const size_t es = ac_elem_size(desc->dtype);
   s->plane_bytes = (size_t)desc->pitch_x * es * (d3 ? (size_t)desc->ny : 1);
   s->part.resize(parts);
+  // several parts step concurrently, each on its own stream, forked from and
+  // joined to the slab's stream around every block of steps
+  if (parts > 1 && cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    s->fork = nullptr;
+    slab_free(s);
+    return sfail(AC_ERR_CUDA, "event creation failed");
+  }
   for (int p = 0; p < parts; ++p) {
     SlabPart &sp = s->part[p];
     sp.plan = plan[p];
+    if (parts > 1 && (cudaStreamCreateWithFlags(&sp.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&sp.done, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      slab_free(s);
+      return sfail(AC_ERR_CUDA, "slab %d: stream or event creation failed", p);
+    }
     ac_grid_desc ld = *desc;
     const int64_t n_ext = sp.plan.ext_hi - sp.plan.ext_lo;
     if (d3) ld.nz = n_ext; else ld.ny = n_ext;
@@ -117,7 +137,7 @@ extern "C" int ac_slab_create(const ac_grid_desc *desc, int32_t parts, int32_t h
       slab_free(s);
       return sfail(AC_ERR_NOMEM, "slab %d: %zu bytes per field do not fit", p, bytes);
     }
-    rc = ac_create(&ld, sp.phi, sp.ws, cuda_stream, &sp.ctx);
+    rc = ac_create(&ld, sp.phi, sp.ws, parts > 1 ? (void *)sp.stream : cuda_stream, &sp.ctx);
     if (rc) {
       slab_free(s);
       return rc;
@@ -183,11 +203,25 @@ static int slab_issue(ac_slab *s, int64_t n) {
       int rc = exchange(s);
       if (rc) return rc;
     }
-    for (SlabPart &p : s->part) {
-      int rc = ac_step(p.ctx, b);
+    if (s->parts == 1) {
+      int rc = ac_step(s->part[0].ctx, b);
       if (rc) return rc;
+    } else {
+      if (cudaEventRecord(s->fork, s->stream) != cudaSuccess)
+        return sfail(AC_ERR_CUDA, "fork event failed");
+      for (SlabPart &p : s->part) {
+        if (cudaStreamWaitEvent(p.stream, s->fork, 0) != cudaSuccess)
+          return sfail(AC_ERR_CUDA, "stream wait failed");
+        int rc = ac_step(p.ctx, b);
+        if (rc) return rc;
+        if (cudaEventRecord(p.done, p.stream) != cudaSuccess)
+          return sfail(AC_ERR_CUDA, "join event failed");
+      }
+      for (SlabPart &p : s->part)
+        if (cudaStreamWaitEvent(s->stream, p.done, 0) != cudaSuccess)
+          return sfail(AC_ERR_CUDA, "stream wait failed");
+      s->fresh = false;
     }
-    if (s->parts > 1) s->fresh = false;
     n -= b;
   }
   return AC_OK;

@@ -110,6 +110,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                "r"(bytes)
                : "memory");
 }
+// Programmatic dependent launch (a kernel launched with the programmatic
+// stream serialization attribute): launch_dependents lets the next such
+// kernel of the stream be scheduled once every CTA of this grid has issued it
+// (or exited); wait blocks until the previous kernel of the stream has
+// completed and its memory operations are visible.  Without the attribute
+// both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // One arrival (release semantics at CTA scope) on an mbarrier.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

@@ -38,36 +38,34 @@ __device__ __forceinline__ void step3d_cell(const T *__restrict__ src, T *__rest
   dst[k * plane + j * g.pitch + i] = from_c<T>(ac_update<C>(p, nsum, C(-6), C(g.alpha), C(g.beta)));
 }
 
-// one thread per x, grid-stride loops over y and z (see cell_grid)
-template <typename T>
+// one thread per x; y and z as for_cell_yz (see cell_grid)
+template <typename T, bool TALL>
 __global__ void __launch_bounds__(256) step2d_direct(const T *__restrict__ src,
                                                      T *__restrict__ dst, GridParams g) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.nx) return;
-  for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
-       j += (int64_t)gridDim.y * blockDim.y)
-    step2d_cell(src, dst, g, i, j);
+  for_cell_yz<TALL>(g, [&](int64_t j, int64_t) { step2d_cell(src, dst, g, i, j); });
 }
 
-template <typename T>
+template <typename T, bool TALL>
 __global__ void __launch_bounds__(256) step3d_direct(const T *__restrict__ src,
                                                      T *__restrict__ dst, GridParams g) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.nx) return;
-  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
-    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
-         j += (int64_t)gridDim.y * blockDim.y)
-      step3d_cell(src, dst, g, i, j, k);
+  for_cell_yz<TALL>(g, [&](int64_t j, int64_t k) { step3d_cell(src, dst, g, i, j, k); });
 }
 
 template <typename T>
 static cudaError_t direct_t(int ndim, const GridParams &g, const void *src, void *dst,
                             cudaStream_t s) {
   const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
+  const bool tall = cell_grid_tall(g);
   if (ndim == 2) {
-    step2d_direct<T><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
+    if (tall) step2d_direct<T, true><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
+    else step2d_direct<T, false><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
   } else {
-    step3d_direct<T><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
+    if (tall) step3d_direct<T, true><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
+    else step3d_direct<T, false><<<grid, block, 0, s>>>((const T *)src, (T *)dst, g);
   }
   return cudaGetLastError();
 }

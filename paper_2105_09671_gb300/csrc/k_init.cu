@@ -79,33 +79,30 @@ __device__ __forceinline__ void sphere_cell(T *__restrict__ phi, const GridParam
   phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
 }
 
-// one thread per x, grid-stride loops over y and z (see cell_grid)
-template <typename T>
+// one thread per x; y and z as for_cell_yz (see cell_grid)
+template <typename T, bool TALL>
 __global__ void init_sphere_k(T *__restrict__ phi, GridParams g, double h, double lx, double ly,
                               double lz, double cx, double cy, double cz, double r0,
                               double width) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.nx) return;
-  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
-    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
-         j += (int64_t)gridDim.y * blockDim.y)
-      sphere_cell(phi, g, i, j, k, h, lx, ly, lz, cx, cy, cz, r0, width);
+  for_cell_yz<TALL>(g, [&](int64_t j, int64_t k) {
+    sphere_cell(phi, g, i, j, k, h, lx, ly, lz, cx, cy, cz, r0, width);
+  });
 }
 
-template <typename T>
+template <typename T, bool TALL>
 __global__ void init_random_k(T *__restrict__ phi, GridParams g, uint64_t seed, double amp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.nx) return;
-  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
-    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
-         j += (int64_t)gridDim.y * blockDim.y) {
-      const uint64_t c = (uint64_t)((k * g.ny + j) * g.nx + i);
-      const uint64_t z = splitmix64_at(seed, c);
-      const double u = (double)(z >> 11) * 0x1.0p-53;
-      const double r = __dsub_rn(__dmul_rn(2.0, u), 1.0);
-      const double v = __dmul_rn(amp, r);
-      phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
-    }
+  for_cell_yz<TALL>(g, [&](int64_t j, int64_t k) {
+    const uint64_t c = (uint64_t)((k * g.ny + j) * g.nx + i);
+    const uint64_t z = splitmix64_at(seed, c);
+    const double u = (double)(z >> 11) * 0x1.0p-53;
+    const double r = __dsub_rn(__dmul_rn(2.0, u), 1.0);
+    const double v = __dmul_rn(amp, r);
+    phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(v);
+  });
 }
 
 // Polar angle of the star (Section 3.1): atan(v/u) for u > 0, pi + atan(v/u)
@@ -167,28 +164,28 @@ __device__ double shape_value(int kind, int ndim, double x, double y, double z, 
   return tanh_ratio(-d, w);
 }
 
-template <typename T>
+template <typename T, bool TALL>
 __global__ void init_shape_k(T *__restrict__ phi, GridParams g, int kind, int ndim, double h,
                              double lx, double ly, double lz, double p0, double p1, double width) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.nx) return;
   const double x = __dadd_rn(lx, __dmul_rn(__dadd_rn((double)i, 0.5), h));
-  for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
-    for (int64_t j = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; j < g.ny;
-         j += (int64_t)gridDim.y * blockDim.y) {
-      const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));
-      const double z = __dadd_rn(lz, __dmul_rn(__dadd_rn((double)k, 0.5), h));
-      phi[(k * g.ny + j) * g.pitch + i] =
-          from_f64<T>(shape_value(kind, ndim, x, y, z, p0, p1, width));
-    }
+  for_cell_yz<TALL>(g, [&](int64_t j, int64_t k) {
+    const double y = __dadd_rn(ly, __dmul_rn(__dadd_rn((double)j, 0.5), h));
+    const double z = __dadd_rn(lz, __dmul_rn(__dadd_rn((double)k, 0.5), h));
+    phi[(k * g.ny + j) * g.pitch + i] = from_f64<T>(shape_value(kind, ndim, x, y, z, p0, p1, width));
+  });
 }
 
 template <typename T>
 static cudaError_t shape_t(const GridParams &g, void *phi, int kind, int ndim, double h,
                            const double *lo, double p0, double p1, double eps, cudaStream_t s) {
   const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
-  init_shape_k<T><<<grid, block, 0, s>>>((T *)phi, g, kind, ndim, h, lo[0], lo[1], lo[2], p0, p1,
-                                         sqrt(2.0) * eps);
+  const double w = sqrt(2.0) * eps;
+  if (cell_grid_tall(g))
+    init_shape_k<T, true><<<grid, block, 0, s>>>((T *)phi, g, kind, ndim, h, lo[0], lo[1], lo[2], p0, p1, w);
+  else
+    init_shape_k<T, false><<<grid, block, 0, s>>>((T *)phi, g, kind, ndim, h, lo[0], lo[1], lo[2], p0, p1, w);
   return cudaGetLastError();
 }
 
@@ -208,8 +205,12 @@ static cudaError_t sphere_t(const GridParams &g, void *phi, double h, const doub
                             const double *c, double r0, double eps, cudaStream_t s) {
   const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
   const double width = sqrt(2.0) * eps;
-  init_sphere_k<T><<<grid, block, 0, s>>>((T *)phi, g, h, lo[0], lo[1], lo[2], c[0], c[1], c[2],
-                                          r0, width);
+  if (cell_grid_tall(g))
+    init_sphere_k<T, true><<<grid, block, 0, s>>>((T *)phi, g, h, lo[0], lo[1], lo[2], c[0], c[1], c[2],
+                                                  r0, width);
+  else
+    init_sphere_k<T, false><<<grid, block, 0, s>>>((T *)phi, g, h, lo[0], lo[1], lo[2], c[0], c[1], c[2],
+                                                   r0, width);
   return cudaGetLastError();
 }
 
@@ -217,7 +218,8 @@ template <typename T>
 static cudaError_t random_t(const GridParams &g, void *phi, uint64_t seed, double amp,
                             cudaStream_t s) {
   const dim3 block(kCellBlockX, kCellBlockY), grid = cell_grid(g);
-  init_random_k<T><<<grid, block, 0, s>>>((T *)phi, g, seed, amp);
+  if (cell_grid_tall(g)) init_random_k<T, true><<<grid, block, 0, s>>>((T *)phi, g, seed, amp);
+  else init_random_k<T, false><<<grid, block, 0, s>>>((T *)phi, g, seed, amp);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,22 @@ Stream3DGeom stream3d_geom(int dtype, int k, int tile);
 // z, with y and z capped at CUDA's 65535 blocks per grid dimension; the
 // kernels cover the rest of y and z by grid-stride loops.
 constexpr unsigned kCellBlockX = 64, kCellBlockY = 4;
+// Whether cell_grid leaves y or z to the kernels' grid-stride loops.
+inline bool cell_grid_tall(const GridParams &g) {
+  return (g.ny + kCellBlockY - 1) / kCellBlockY > 65535 || g.nz > 65535;
+}
+// Calls f(j, k) for this thread's (y, z) cells: once (the grid covers the
+// domain, no loop), or by grid-stride loops for TALL grids.
+template <bool TALL, typename F>
+__device__ __forceinline__ void for_cell_yz(const GridParams &g, F &&f) {
+  const int64_t j0 = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  if constexpr (!TALL) {
+    if (j0 < g.ny) f(j0, (int64_t)blockIdx.z);
+  } else {
+    for (int64_t k = blockIdx.z; k < g.nz; k += gridDim.z)
+      for (int64_t j = j0; j < g.ny; j += (int64_t)gridDim.y * blockDim.y) f(j, k);
+  }
+}
 inline dim3 cell_grid(const GridParams &g) {
   return dim3((unsigned)((g.nx + kCellBlockX - 1) / kCellBlockX),
               (unsigned)std::min<int64_t>((g.ny + kCellBlockY - 1) / kCellBlockY, 65535),

@@ -105,3 +105,34 @@ def test_sphere_512_sampled(dtype):
     tol = TOL_MAXABS["f32"] if dtype == "f32" else 2e-3  # one FP16 rounding per pass
     _check_samples(phi0.astype(np.float64), out.astype(np.float64), w.h, w.eps, w.dt, n, pts, tol)
     assert e1 < e0
+
+
+def test_sphere_512_job_graph_replay_equals_plain_launches():
+    # the benchmark's job exactly: device initial condition, 2000 steps of the
+    # default schedule replayed as one CUDA graph; bit for bit the launches
+    # issued one by one, and the sphere shrinks by the 3D mean-curvature law
+    # R^2 = R0^2 - 4t (Section 3.1) to within 10 % of the change
+    import torch
+    w = wl.SPHERE_512
+    out = []
+    r2 = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        sim = ac.Simulation(w.shape, w.h, w.eps, w.dt, dtype="f32", stream=s)
+        try:
+            sim.init_sphere(r0=w.r0)
+            v0 = sim.phase_volume()
+            sim.set_graph(graph)
+            sim.step(w.steps)
+            v1 = sim.phase_volume()
+            assert sim.status() == ac.AC_OK
+            out.append(sim.phi.clone())
+            r2.append(((3 * v0 / (4 * np.pi)) ** (2 / 3), (3 * v1 / (4 * np.pi)) ** (2 / 3)))
+        finally:
+            sim.close()
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], out[1])
+    assert bool(torch.isfinite(out[1]).all())
+    t = w.steps * w.dt
+    drop = r2[1][0] - r2[1][1]
+    assert abs(drop - 4 * t) <= 0.1 * 4 * t, f"R^2 drop {drop:.4e} against 4t = {4 * t:.4e}"

@@ -76,7 +76,14 @@ typedef enum {
  *   dt       time step > 0.  The paper uses dt = 0.1 h^2.  The library
  *            requires dt <= h^2 / (2 ndim) (stability of the explicit
  *            Laplacian) and dt <= eps^2 (reaction step alpha = dt/eps^2
- *            at most 1); anything else is AC_ERR_INVALID.
+ *            at most 1); anything else is AC_ERR_INVALID.  Within those
+ *            limits the scheme keeps |phi| <= 1 (a discrete maximum
+ *            principle, and with it the monotone energy decrease) only
+ *            while the centre coefficient 1 + alpha - 3 alpha phi^2 -
+ *            2 ndim dt/h^2 stays positive, i.e. alpha < (1 - 2 ndim dt/h^2)/2
+ *            (0.2 in 3D and 0.3 in 2D at dt = 0.1 h^2); beyond that (eps
+ *            well below h) a run can overshoot +-1, as the same scheme does
+ *            in FP64.
  */
 typedef struct {
   int32_t ndim;

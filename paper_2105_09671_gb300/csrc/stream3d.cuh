@@ -108,6 +108,12 @@ struct S3Geom {
   static constexpr int STAGE_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;  // TMA dst alignment
   static constexpr int LVL_BYTES = TX * TY * (int)sizeof(C);
+  // Level buffers of 8-cell vectors (FP16 storage) are split in two regions
+  // of 4-value halves (LHALF elements apart, LROW elements per row), so that
+  // each lane's 16-byte read or write is one of 32 consecutive 16-byte words
+  // (the 32-byte vectors side by side conflict two ways in shared memory).
+  static constexpr bool LSPLIT = V == 8 && std::is_same_v<C, float>;
+  static constexpr int LROW = LSPLIT ? TX / 2 : TX, LHALF = LSPLIT ? TX * TY / 2 : 0;
   static constexpr int LVL_TOTAL = (K > 1 ? 3 * (K - 1) * LVL_BYTES : 0);  // 3 planes per level
   // D TMA stages (3 or 6; the planes in flight hide HBM latency): 6 at
   // k = 1, else per type and tile as measured on GB300 at 512^3 (six pay
@@ -179,6 +185,27 @@ __device__ __forceinline__ void st_vec_c(double *buf, int idx, const double *in)
 #pragma unroll
   for (int i = 0; i < V; i += 2)
     *reinterpret_cast<double2 *>(buf + idx + i) = make_double2(in[i], in[i + 1]);
+}
+
+// A vector of V compute values in a level buffer (split layout: two halves
+// Gm::LHALF elements apart).
+template <typename Gm, typename C>
+__device__ __forceinline__ void ld_lvl(const C *buf, int idx, C *out) {
+  if constexpr (Gm::LSPLIT) {
+    ld_vec_c<Gm::V / 2>(buf, idx, out);
+    ld_vec_c<Gm::V / 2>(buf + Gm::LHALF, idx, out + Gm::V / 2);
+  } else {
+    ld_vec_c<Gm::V>(buf, idx, out);
+  }
+}
+template <typename Gm, typename C>
+__device__ __forceinline__ void st_lvl(C *buf, int idx, const C *in) {
+  if constexpr (Gm::LSPLIT) {
+    st_vec_c<Gm::V / 2>(buf, idx, in);
+    st_vec_c<Gm::V / 2>(buf + Gm::LHALF, idx, in + Gm::V / 2);
+  } else {
+    st_vec_c<Gm::V>(buf, idx, in);
+  }
 }
 
 template <typename T, int K, bool FASTX, int TILE>
@@ -309,6 +336,15 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
     const int ysn = max(r0 - 1, rlo) * TX + qc * V;   // row below the group
     const int ynn = min(r0 + R, rhi) * TX + qc * V;   // row above the group
     const int eoff = esm ? own + (lsm ? -1 : V) : own;  // the x neighbour read from shared memory
+    // the same places in the level buffers' layout
+    constexpr int LROW = Gm::LROW, LHALF = Gm::LHALF, LV = Gm::LSPLIT ? V / 2 : V;
+    const int lown = r0 * LROW + qc * LV;
+    const int lysn = max(r0 - 1, rlo) * LROW + qc * LV;
+    const int lynn = min(r0 + R, rhi) * LROW + qc * LV;
+    const int leoff = !Gm::LSPLIT ? eoff
+                      : !esm      ? lown
+                      : lsm       ? LHALF + lown - LV + (LV - 1)   // last cell of the vector on the left
+                                  : lown + LV;                     // first cell of the vector on the right
     const int gx0 = bx + qc * V;
     const bool lfix = gx0 == 0;               // element 0 is the x = 0 face
     const bool rfix = gx0 + V - 1 == nx - 1;  // element V-1 is the x = nx-1 face
@@ -356,10 +392,10 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
         if (l == K - 1 && hw) break;  // halo warps: no last level
         if (l > 0) {
           const C *cb = lvl + ((l - 1) * 3 + LR) * PLANE;
-          ld_vec_c<V>(cb, ysn, ys[l]);
-          ld_vec_c<V>(cb, ynn, yn[l]);
+          ld_lvl<Gm>(cb, lysn, ys[l]);
+          ld_lvl<Gm>(cb, lynn, yn[l]);
 #pragma unroll
-          for (int i = 0; i < R; ++i) ev[l][i] = esm ? cb[eoff + i * TX] : C(0);
+          for (int i = 0; i < R; ++i) ev[l][i] = esm ? cb[leoff + i * LROW] : C(0);
         }
         const int Z = lo0 + t - (l + 1);  // plane of level l+1 formed now
         if constexpr (BND) {
@@ -418,7 +454,7 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
           if (l + 1 < K) {
 #pragma unroll
             for (int e = 0; e < V; ++e) ring[l + 1 < K ? l + 1 : 0][SN][i][e] = out[e];
-            if (qv) st_vec_c<V>(lvl + (l * 3 + LW) * PLANE, own + i * TX, out);
+            if (qv) st_lvl<Gm>(lvl + (l * 3 + LW) * PLANE, lown + i * LROW, out);
           } else {
             // the address is formed by every thread and only the store is
             // predicated (one predicated 16-byte store, no branch)

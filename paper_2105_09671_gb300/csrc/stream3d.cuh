@@ -336,15 +336,17 @@ __global__ void __launch_bounds__(S3Geom<T, K, TILE>::NT, S3Geom<T, K, TILE>::MI
     const int ysn = max(r0 - 1, rlo) * TX + qc * V;   // row below the group
     const int ynn = min(r0 + R, rhi) * TX + qc * V;   // row above the group
     const int eoff = esm ? own + (lsm ? -1 : V) : own;  // the x neighbour read from shared memory
-    // the same places in the level buffers' layout
+    // The same places in the level buffers' layout.  Split layout: a
+    // vector's first LV values in region 0, its last LV in region 1; the
+    // left neighbour cell (last of the vector on the left) is the last value
+    // of that vector's region-1 half, the right one (first of the vector on
+    // the right) the first value of its region-0 half.
     constexpr int LROW = Gm::LROW, LHALF = Gm::LHALF, LV = Gm::LSPLIT ? V / 2 : V;
     const int lown = r0 * LROW + qc * LV;
     const int lysn = max(r0 - 1, rlo) * LROW + qc * LV;
     const int lynn = min(r0 + R, rhi) * LROW + qc * LV;
-    const int leoff = !Gm::LSPLIT ? eoff
-                      : !esm      ? lown
-                      : lsm       ? LHALF + lown - LV + (LV - 1)   // last cell of the vector on the left
-                                  : lown + LV;                     // first cell of the vector on the right
+    int leoff = eoff;
+    if constexpr (Gm::LSPLIT) leoff = !esm ? lown : lsm ? LHALF + lown - 1 : lown + LV;
     const int gx0 = bx + qc * V;
     const bool lfix = gx0 == 0;               // element 0 is the x = 0 face
     const bool rfix = gx0 + V - 1 == nx - 1;  // element V-1 is the x = nx-1 face

@@ -270,13 +270,20 @@ static bool wide_default(const ac_grid_desc *d) {
   return d->ndim == 2 && d->dtype == AC_F32 && (double)d->nx * (double)d->ny >= kWideStripCells;
 }
 
+// 2D FP16-storage grids from this many cells take k = 6 (measured on GB300:
+// 1827 / 2196 Gcell-updates/s at 4096^2 / 8192^2 against 1657 / 1906 at
+// k = 4; at 2048^2 and below k = 4 or 5 is faster).
+constexpr double kDeepHalfCells = 4096.0 * 4096.0;
+
 int ac_default_depth(const ac_grid_desc *d) {
   // FP64 is bound by the GPU's FP64 rate, where the redundant halo work of
   // temporal blocking costs more than the memory traffic it saves: one step
   // per launch.  FP32 / FP16 storage stream with k > 1 (measured best on
-  // GB300: 3D k = 2; 2D k = 4, or 6 with the 8-cell FP32 strips).
+  // GB300: 3D k = 2; 2D k = 4, or 6 with the 8-cell FP32 strips and for
+  // large FP16-storage grids).
   if (d->dtype == AC_F64) return 1;
   if (d->ndim == 3) return 2;
+  if (d->dtype == AC_F16S && (double)d->nx * (double)d->ny >= kDeepHalfCells) return 6;
   return wide_default(d) ? 6 : 4;
 }
 

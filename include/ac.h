@@ -530,9 +530,9 @@ int ac_slab_plan(int64_t extent, int32_t parts, int32_t halo, ac_slab_part *out)
 /* In-process slabs on the current device: `parts` contexts over extended
  * slabs that this call allocates (field and workspace each; freed by
  * ac_slab_destroy).  halo = 0 takes twice the default temporal-block depth
- * of the grid (3D: 4; 2D: 8, or 12 for FP32 grids of at least 1024^2
- * cells and FP16-storage grids of at least 4096^2 cells; FP64: 2), so that
- * a block is two passes.  All work is ordered on
+ * of the grid (3D: 4; 2D: 8, 10 for FP32 grids of at least 1024^2 cells,
+ * 12 for FP32 and FP16-storage grids of at least 4096^2 cells; FP64: 2), so
+ * that a block is two passes.  All work is ordered on
  * cuda_stream: with several parts each part steps on a stream of its own
  * (created here), forked from cuda_stream before every block of steps and
  * joined back after it, so the parts' launches may run concurrently; halo

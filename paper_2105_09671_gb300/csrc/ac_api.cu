@@ -257,14 +257,17 @@ static bool schedule_ok(const ac_ctx *c, int variant, int k, int tile = 0) {
   return false;
 }
 
-// 2D FP32 grids from this many cells on take the 8-cell strips by default:
-// measured on GB300, 4096^2 at k = 6 with 8-cell strips runs at 1634
-// Gcell-updates/s against 1485 for 4-cell strips at k = 4, 8192^2 at 2006
-// against 1841; grids of a few hundred cells per side, which are bound by
-// launch latency and leave most lanes of a 240-column strip idle, keep the
-// 4-cell strips (512 grids of 64^2 .. 1024^2 stepped one by one: 3.2 s
+// 2D FP32 grids from kWideStripCells cells on take the 8-cell strips at
+// k = 6 by default: measured on GB300, 4096^2 runs at 1636 Gcell-updates/s
+// (1712 graph-replayed) against 1573 for 4-cell strips at k = 5, 8192^2 at
+// 2006 against 1841 (k = 4).  Below that the 240-column strips leave too few
+// warps busy: 2048^2 runs at 876 with them against 1021 (k = 5) and 1090
+// (k = 8) with 4-cell strips, 1024^2 at 236 against 365 (k = 5), so grids
+// from kMidCells take 4-cell strips at k = 5, smaller ones k = 4 (bound by
+// launch latency; 512 grids of 64^2 .. 1024^2 stepped one by one: 3.2 s
 // against 4.5 s with the wide strips).
-constexpr double kWideStripCells = 1024.0 * 1024.0;
+constexpr double kWideStripCells = 4096.0 * 4096.0;
+constexpr double kMidCells = 1024.0 * 1024.0;
 
 static bool wide_default(const ac_grid_desc *d) {
   return d->ndim == 2 && d->dtype == AC_F32 && (double)d->nx * (double)d->ny >= kWideStripCells;
@@ -283,8 +286,10 @@ int ac_default_depth(const ac_grid_desc *d) {
   // large FP16-storage grids).
   if (d->dtype == AC_F64) return 1;
   if (d->ndim == 3) return 2;
-  if (d->dtype == AC_F16S && (double)d->nx * (double)d->ny >= kDeepHalfCells) return 6;
-  return wide_default(d) ? 6 : 4;
+  const double cells = (double)d->nx * (double)d->ny;
+  if (d->dtype == AC_F16S && cells >= kDeepHalfCells) return 6;
+  if (wide_default(d)) return 6;
+  return d->dtype == AC_F32 && cells >= kMidCells ? 5 : 4;
 }
 
 static void default_schedule(const ac_ctx *c, int *variant, int *k) {
@@ -307,7 +312,7 @@ static void effective_schedule(const ac_ctx *c, int *variant, int *k) {
 // 1114 Gcell-updates/s at k = 2); k = 3 needs the register room of four rows
 // per thread with half the threads (tile 2).
 static int default_tile(const ac_ctx *c, int k) {
-  // 2D FP32 grids from 1024^2 cells on: strips of 8 cells per lane wherever
+  // 2D FP32 grids from 4096^2 cells on: strips of 8 cells per lane wherever
   // they are offered (k <= 6; see kWideStripCells)
   if (c->d.ndim == 2) return wide_default(&c->d) && k <= 6 ? 1 : 0;
   if (c->d.dtype == AC_F64) return k == 1 ? 0 : 2;

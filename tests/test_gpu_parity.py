@@ -213,10 +213,12 @@ def test_tile_selection_api():
     sim2 = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim3 = ac.Simulation((8, 16, 16), 1 / 16, 0.1, 1e-4, dtype="f32")
     sim2h = ac.Simulation((16, 16), 1 / 16, 0.1, 1e-4, dtype="f16s")
-    big = ac.Simulation((1024, 1024), 1 / 1024, 4 / 1024, 0.1 / 1024 ** 2, dtype="f32")
+    big = ac.Simulation((4096, 4096), 1 / 4096, 4 / 4096, 0.1 / 4096 ** 2, dtype="f32")
+    mid = ac.Simulation((1024, 1024), 1 / 1024, 4 / 1024, 0.1 / 1024 ** 2, dtype="f32")
     try:
         assert sim2.tile() == 0 and sim2.schedule() == (ac.AC_VARIANT_STREAM, 4)
-        assert big.tile() == 1 and big.schedule() == (ac.AC_VARIANT_STREAM, 6)  # 8-cell strips from 1024^2
+        assert big.tile() == 1 and big.schedule() == (ac.AC_VARIANT_STREAM, 6)  # 8-cell strips from 4096^2
+        assert mid.tile() == 0 and mid.schedule() == (ac.AC_VARIANT_STREAM, 5)  # 4-cell strips, k = 5
         sim2.set_tile(0)
         sim2.set_tile(1)             # FP32 2D: strips of 8 cells per lane
         assert sim2.tile() == 1
@@ -239,6 +241,7 @@ def test_tile_selection_api():
         assert sim3.tile() in range(ac.AC_NUM_TILES_3D)
     finally:
         big.close()
+        mid.close()
         sim2h.close()
         sim2.close()
         sim3.close()
